@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark of the SaCD hot path on one GB300 (or N independent replicas under torchrun).
+
+A "step" is one SaCD outer iteration (the mode steps 0..N-1: MTTKRP, H/L, gradient and
+importance, selection and update, Gram refresh) followed by the objective/fit evaluation, on the
+workload's tensor resident in HBM. value = mode steps per second over the timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+Prints one JSON line (rank 0). The reference arm (--impl reference) times the FP64 CPU oracle
+on the host cores, on the same workload and metric.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "zipf1.1-50000x20000x500-5M-r32"
+L2_BYTES = 129 * 2**20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def mttkrp_bytes(w, nnz, mode):
+    """Algorithmic bytes of one MTTKRP launch (COO model): per nonzero its value, its N
+    coordinates and the N-1 gathered factor rows (R columns each), plus the I_n x R output."""
+    s = 2 if w.precision == "bf16" else 4
+    N = w.nmodes
+    return nnz * (4 + 4 * N + (N - 1) * w.rank * s) + w.dims[mode] * w.rank * 4
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_from_profile(src_sha):
+    """DRAM bytes per MTTKRP launch from the committed ncu summary, if it was taken on the
+    current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "mttkrp_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("mttkrp_source_sha256") != src_sha:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def cpu_baseline_child(workload, nsteps):
+    """Run in a fresh single-threaded process: time the FP64 oracle on the workload."""
+    from oracle import sacd_oracle as O
+    from paper_2003_03572_gb300 import synth
+
+    w = synth.WORKLOADS[workload]
+    idx, vals, init = synth.make_workload(w)
+    o = O.SaCDOracle(w.dims, idx, vals, init)  # one-time coalescing, not timed
+    t = time.perf_counter()
+    for s in range(nsteps):
+        o.mode_step(s % w.nmodes)
+    dt = time.perf_counter() - t
+    print(json.dumps({"steps": nsteps, "seconds": dt}))
+
+
+def run_cpu_baseline(workload, nsteps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", "--workload", workload,
+                        "--steps", str(nsteps)], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        return None
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["steps"] / d["seconds"], d
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reference_arm(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import sacd_oracle as O
+    from paper_2003_03572_gb300 import synth
+
+    w = synth.WORKLOADS[args.workload]
+    idx, vals, init = synth.make_workload(w)
+    o = O.SaCDOracle(w.dims, idx, vals, init)
+    step = 0
+    for _ in range(args.warmup):
+        o.mode_step(step % w.nmodes)
+        step += 1
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        o.mode_step(step % w.nmodes)
+        step += 1
+    dt = time.perf_counter() - t
+    v = args.steps / dt
+    sample = (f"{args.steps} FP64 oracle mode steps (cycling modes) on the full workload, "
+              f"after {args.warmup} warm-up mode steps; one process")
+    line = {
+        "impl": "reference",
+        "metric": "SaCD mode-steps/s",
+        "value": v,
+        "unit": "mode-steps/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "dims": list(w.dims), "nnz": w.nnz, "rank": w.rank, "step": "one mode step"},
+        "cpu_baseline": {"value": v, "unit": "mode-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "mode-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_2003_03572_gb300 import sacd as S
+    from paper_2003_03572_gb300 import synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    w = synth.WORKLOADS[args.workload]
+    idx, vals, init = synth.make_workload(w)
+    N = w.nmodes
+    prec = S.SACD_BF16_GATHER if w.precision == "bf16" else S.SACD_FP32
+    stream = torch.cuda.Stream(device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---------------------------------------------------------------- device-resident timing
+    g = S.SaCD(w.dims, idx, vals, w.rank, init, precision=prec, stream=stream.cuda_stream)
+    info = g.info
+    nnz = info["nnz"]
+    for _ in range(args.warmup):
+        g.iterate(1)
+        g.fit()
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clk = ClockSampler(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.iterate(1)
+        obj, fit = g.fit()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps * N / (ms / 1e3)
+
+    # ---------------------------------------------------------------- per-kernel timing
+    S.sacd_profile_enable(g.ctx, True)
+    for _ in range(args.steps):
+        g.iterate(1)
+        g.fit()
+    stats = S.sacd_profile_read(g.ctx)
+    S.sacd_profile_enable(g.ctx, False)
+    launches = sum(v[0] for v in stats.values())
+    mt_launches, mt_ms = stats["mttkrp"]
+    tot_bytes = args.steps * sum(mttkrp_bytes(w, nnz, n) for n in range(N))
+    achieved = tot_bytes / (mt_ms / 1e3) / 1e9 if mt_ms > 0 else None
+    peak, peak_kind = peaks()
+    src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2003_03572_gb300", "csrc", "mttkrp.cu"), "rb").read()).hexdigest()
+    traffic = traffic_from_profile(src_sha)
+    kernel_ms = {k: v[1] for k, v in stats.items()}
+    total_kernel_ms = sum(kernel_ms.values())
+    g.close()
+
+    if args.kernels_only:  # short run for a profiler: device-resident steps only
+        if rank == 0:
+            print(json.dumps({"kernels_only": True, "value": value, "unit": "mode-steps/s",
+                              "kernel_ms_per_step": {k: v / args.steps for k, v in kernel_ms.items()}}))
+        return 0
+
+    # ---------------------------------------------------------------- end to end, host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_idx = [pin(idx[n]) for n in range(N)]
+    h_vals = pin(vals)
+    h_init = [pin(a) for a in init]
+    h_out = [torch.empty(a.shape, dtype=torch.float32).pin_memory() for a in init]
+    iters = w.iters
+    e2e_times = []
+    for rep in range(max(args.e2e_reps, 1) + 1):
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        ctx = S.sacd_create(w.dims, [t.numpy() for t in h_idx], h_vals.numpy(), w.rank,
+                            [t.numpy() for t in h_init], precision=prec, stream=stream.cuda_stream)
+        S.sacd_iterate(ctx, iters)
+        S.sacd_fit(ctx)
+        for n in range(N):
+            S.sacd_get_factor(ctx, n, h_out[n].numpy())
+        S.sacd_destroy(ctx)
+        t1 = time.perf_counter()
+        if rep > 0:  # first solve is a warm-up (allocator, graph instantiation)
+            e2e_times.append(t1 - t0)
+    e2e_s = statistics.median(e2e_times)
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ws * N * iters / e2e_s
+    h2d = int(len(vals) * (4 * N + 4) + sum(a.nbytes for a in init))
+    d2h = int(sum(a.nbytes for a in init) + 16)
+
+    # ---------------------------------------------------------------- CPU baseline (rank 0, N=1)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        res = run_cpu_baseline(args.workload, N)
+        if res:
+            v, d = res
+            cpu = {"value": v, "unit": "mode-steps/s", "cores": 1, "kind": "oracle",
+                   "sample": f"one SaCD iteration ({N} mode steps) of the FP64 oracle on the full workload, "
+                             f"single-threaded, after its one-time coalescing ({d['seconds']:.1f} s)"}
+
+    if rank == 0:
+        csf_bytes = nnz * (4 * N + 4) * N
+        line = {
+            "metric": "SaCD mode-steps/s",
+            "value": value,
+            "unit": "mode-steps/s",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32" if prec == S.SACD_FP32 else "bf16-gather/f32",
+            "data": "synthetic",
+            "config": {
+                "workload": w.name,
+                "dims": list(w.dims),
+                "nnz": nnz,
+                "rank": w.rank,
+                "step": "one SaCD iteration (all modes) + objective/fit",
+                "l2": f"inputs larger than L2: {csf_bytes / 1e6:.0f} MB of sorted nonzeros per step vs "
+                      f"{L2_BYTES / 1e6:.0f} MB L2",
+                "parallelism": "replicas" if ws > 1 else "single GPU",
+                "final_fit": fit,
+            },
+            "roofline": {
+                "bound": "hbm",
+                "kernel": "mttkrp",
+                "achieved": achieved,
+                "peak": peak,
+                "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": traffic,
+                "bytes_model": "COO model: nnz*(4 + 4N + (N-1)*R*s) + I_n*R*4 per launch",
+                "mttkrp_share": mt_ms / total_kernel_ms if total_kernel_ms else None,
+            },
+            "kernel_ms_per_step": {k: v / args.steps for k, v in kernel_ms.items()},
+            "gpu_launches": int(launches),
+            "e2e": {
+                "value": e2e_value,
+                "unit": "mode-steps/s",
+                "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "step": f"one full solve from pinned host COO: create (copy + CSF build) + {iters} iterations "
+                        f"+ fit + factors back",
+                "seconds_per_solve": e2e_s,
+            },
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--e2e-reps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true", help="skip the end-to-end and CPU legs (profiling)")
+    ap.add_argument("--cpu-baseline-child", action="store_true")
+    args = ap.parse_args()
+    if args.cpu_baseline_child:
+        cpu_baseline_child(args.workload, args.steps)
+        return 0
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,208 @@
+/*
+ * sacd.h -- C ABI of libsacd.so: Saturating Coordinate Descent (SaCD) for nonnegative CP
+ * factorisation of sparse N-mode tensors, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Balasubramaniam, Nayak, Yuen, "Efficient Nonnegative Tensor Factorization via
+ * Saturating Coordinate Descent" (ACM TKDD 2020). Algorithm 1; Eq. 9-15 (gradient G and second
+ * derivative H), Eq. 11-13 (nonnegative coordinate update), Eq. 20 (Lipschitz element
+ * importance), Eq. 24-27 (saturation point and total importance), Lemma 2 (gradient fix-up),
+ * Eq. 6-8 (objective).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns a sacd_status. On any error a thread-local message is available from
+ *    sacd_last_error(). No C++ exception crosses this ABI.
+ *  - Host pointers passed in are owned by the caller and are only read during the call (the
+ *    library copies what it keeps). A sacd_ctx owns all device memory it allocates; it is
+ *    released by sacd_destroy().
+ *  - All device work of a context runs on one CUDA stream (the caller's, or one the context
+ *    creates). Calls on one context must not be made concurrently from several threads.
+ *  - A CUDA error (including an asynchronous fault seen at a later synchronisation) returns
+ *    SACD_ECUDA and poisons the context: afterwards every call but sacd_destroy returns
+ *    SACD_ESTATE.
+ *  - Factor matrices cross the ABI as row-major I_n x R FP32 arrays.
+ */
+#ifndef SACD_H
+#define SACD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SACD_OK = 0,
+  SACD_EINVAL = 1,   /* bad argument: ranges, null pointers, out-of-range indices, bad init */
+  SACD_ENOMEM = 2,   /* device (or pinned host) allocation failed */
+  SACD_ECUDA = 3,    /* CUDA runtime error; the context is poisoned */
+  SACD_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+  SACD_ESTATE = 5    /* call not legal in the context's state (poisoned, wrong mode, ...) */
+} sacd_status;
+
+/* Storage of the factor rows that the MTTKRP gathers. FP32 master factors are kept in both. */
+typedef enum {
+  SACD_FP32 = 0,        /* gather FP32 rows */
+  SACD_BF16_GATHER = 1  /* gather a BF16 mirror of the factors, accumulate in FP32 */
+} sacd_precision;
+
+/* Constant L in the element importance z = -g s - (L/2) s^2 (Eq. 20). */
+typedef enum {
+  SACD_LNORM_FRO = 0,      /* L = ||H||_F (symbol table: ||.|| is the Frobenius norm) */
+  SACD_LNORM_SPECTRAL = 1, /* L = largest eigenvalue of H (H is symmetric positive semidefinite) */
+  SACD_LNORM_GCD = 2       /* L replaced by h_rr per column: the GCD importance of Eq. 18 */
+} sacd_lnorm;
+
+/* Gradient fix-up after a coordinate update u_qr += s within one mode step. */
+typedef enum {
+  SACD_FIXUP_COLUMN_GS = 0, /* g_q. += s * H[r,.]: later columns of row q see the exact gradient */
+  SACD_FIXUP_LEMMA2 = 1     /* Lemma 2 read literally: only g_qr changes (Jacobi within the row) */
+} sacd_fixup;
+
+typedef struct sacd_ctx sacd_ctx; /* opaque */
+
+typedef struct {
+  int32_t nmodes;             /* N, 2 <= N <= 8 */
+  const int64_t* dims;        /* host, N entries, each in [1, 2^31-1] */
+  int64_t nnz;                /* number of COO entries, 0 <= nnz <= 2^31-1 */
+  const int32_t* const* idx;  /* host array of N pointers; idx[n][e] is the 0-based mode-n index */
+  const float* vals;          /* nnz values (any sign; repeated coordinates are summed) */
+  int32_t rank;               /* R, 1 <= R <= 256 */
+  const float* const* init;   /* host array of N pointers to I_n x R row-major FP32, or NULL:
+                                 U[0,1) from `seed`. Values must be finite and >= 0 */
+  uint64_t seed;              /* used only when init == NULL */
+  int32_t precision;          /* sacd_precision */
+  int32_t lnorm;              /* sacd_lnorm */
+  int32_t fixup;              /* sacd_fixup */
+  int32_t inputs_on_device;   /* 0: idx[n], vals, init[n] point to host memory;
+                                 1: they point to device memory of the current device */
+  void* stream;               /* cudaStream_t to run on, or NULL: the context creates its own */
+} sacd_config;
+
+/* Sizes and constants of a context (sacd_get_info). */
+typedef struct {
+  int32_t nmodes;
+  int32_t rank;
+  int32_t rank_padded;        /* row stride of the device factor matrices */
+  int32_t precision;
+  int64_t dims[8];
+  int64_t nnz;                /* distinct coordinates after summing repeats */
+  double norm_x_sq;           /* ||X||^2 in FP64 */
+  int64_t device_bytes;       /* device memory held by the context */
+  int64_t tiles[8];           /* MTTKRP warp tiles per mode */
+  int64_t tile_nnz[8];        /* nonzeros per warp tile per mode */
+  int64_t split_rows[8];      /* rows whose nonzeros straddle a tile boundary, per mode */
+} sacd_info;
+
+/*
+ * sacd_create -- copy a sparse tensor and initial factors to the device and build the per-mode
+ * sorted slice structure (the sets Omega^(n)_q of the symbol table: nonzeros ordered by i_n, then
+ * by the other modes in ascending mode order), summing repeated coordinates in FP32 in input
+ * order. Computes ||X||^2 and the FP64 Gram matrices A_k^T A_k of the initial factors.
+ * Every factor starts "unvisited" (Algorithm 1, k == 1 branch).
+ * On success *out receives the context; on error *out is set to NULL.
+ * Errors: SACD_EINVAL (cfg ranges, an index outside [0, dims[n]), negative or non-finite init),
+ * SACD_ENOMEM, SACD_ECUDA.
+ */
+sacd_status sacd_create(const sacd_config* cfg, sacd_ctx** out);
+
+/*
+ * sacd_mode_step -- one SaCD mode step for factor `mode` (Algorithm 1, one of its three
+ * factor blocks): MTTKRP M = X_(n)(Khatri-Rao of the other factors) (Eq. 9), H = Hadamard of
+ * the other Grams (Eq. 10), L (Algorithm 1), G = A H - M (Eq. 9, 14), z (Eq. 20), ti (Eq. 25),
+ * selection (z > 0 on the first visit, else sp > 0 from Eq. 24 / Eq. 27), the projected
+ * update of the selected elements (Eq. 11-13) with the configured fix-up, z^{k-1} <- z, and
+ * the refreshed FP64 Gram of the updated factor. Enqueued on the context's stream.
+ * n_selected (nullable): if given, the call waits for the step and stores |E|, the number of
+ * selected elements. Errors: SACD_EINVAL (mode out of range), SACD_ECUDA, SACD_ESTATE.
+ */
+sacd_status sacd_mode_step(sacd_ctx* ctx, int32_t mode, int64_t* n_selected);
+
+/*
+ * sacd_iterate -- `iters` outer SaCD iterations, each the mode steps 0..N-1 in order
+ * (Algorithm 1's loop over k). The first call captures one iteration in a CUDA graph and
+ * replays it; nothing is synchronised. Errors: SACD_EINVAL (iters < 0), SACD_ECUDA, SACD_ESTATE.
+ */
+sacd_status sacd_iterate(sacd_ctx* ctx, int32_t iters);
+
+/*
+ * sacd_fit -- objective f = ||X - [[A]]||^2 over all cells (Eq. 6-8), as
+ * ||X||^2 - 2<X, [[A]]> + sum_{r,s} prod_k (A_k^T A_k)_{rs}, in FP64, and
+ * fit = 1 - sqrt(max(f, 0)) / ||X||. Waits for the stream. Either output pointer may be NULL.
+ */
+sacd_status sacd_fit(sacd_ctx* ctx, double* objective, double* fit);
+
+/* sacd_get_factor -- copy factor `mode` (I_n x R row-major FP32) to host_out. Waits. */
+sacd_status sacd_get_factor(sacd_ctx* ctx, int32_t mode, float* host_out);
+
+/*
+ * sacd_set_factor -- replace factor `mode` with host_in (I_n x R row-major FP32, finite, >= 0)
+ * and refresh its Gram (and BF16 mirror). The importance state (z^{k-1}, ti^{k-1}, first
+ * visit) is left as it is. Errors: SACD_EINVAL (mode, bad values), SACD_ECUDA.
+ */
+sacd_status sacd_set_factor(sacd_ctx* ctx, int32_t mode, const float* host_in);
+
+/* Debug taps (sacd_debug_tap `what`). "last step" = the most recent mode step of any mode. */
+typedef enum {
+  SACD_TAP_M = 0,        /* float  I_mode x R   : MTTKRP of `mode` from its most recent step */
+  SACD_TAP_G = 1,        /* float  I_n x R      : gradient at the start of the last step (n = its mode) */
+  SACD_TAP_ZPREV = 2,    /* float  I_mode x R   : z^{k-1} of `mode` (z of its most recent step) */
+  SACD_TAP_MASK = 3,     /* uint8  I_n x R      : selection of the last step (needs sacd_set_debug) */
+  SACD_TAP_H = 4,        /* double R x R        : H of the last step */
+  SACD_TAP_GRAM = 5,     /* double R x R        : A_mode^T A_mode */
+  SACD_TAP_STATE = 6,    /* double 8            : per `mode`: ti^{k-1}, first-visit flag, ti of the
+                                                   last step of `mode`, branch (0 first, 1 Eq. 24,
+                                                   2 Eq. 27), L, |E|, 0, 0 */
+  SACD_TAP_CSF_ROW = 7,  /* int32  nnz          : mode-`mode` sorted row index per nonzero */
+  SACD_TAP_CSF_IDX = 8,  /* int32  (N-1) x nnz  : the other modes' indices, ascending mode order */
+  SACD_TAP_CSF_VAL = 9   /* float  nnz          : values in mode-`mode` sorted order */
+} sacd_tap;
+
+/*
+ * sacd_debug_tap -- copy one piece of device state to host_out (layout per sacd_tap). Waits.
+ * For tests and diagnostics only. Errors: SACD_EINVAL (what/mode), SACD_ESTATE (MASK without
+ * sacd_set_debug(ctx, 1), or G/H/MASK before any step).
+ */
+sacd_status sacd_debug_tap(sacd_ctx* ctx, int32_t what, int32_t mode, void* host_out);
+
+/* sacd_set_debug -- when on, mode steps also record the selection mask (one byte per element). */
+sacd_status sacd_set_debug(sacd_ctx* ctx, int32_t on);
+
+/*
+ * sacd_replay_mask -- make the next mode step of `mode` apply host_mask (uint8 I_mode x R,
+ * nonzero = selected) instead of its own selection, everything else unchanged. For parity
+ * tests that compare the arithmetic with a selection fixed on both sides. NULL clears it.
+ */
+sacd_status sacd_replay_mask(sacd_ctx* ctx, int32_t mode, const uint8_t* host_mask);
+
+/* sacd_get_info -- sizes and constants of the context. */
+sacd_status sacd_get_info(sacd_ctx* ctx, sacd_info* out);
+
+/* sacd_sync -- wait for all work enqueued on the context's stream. */
+sacd_status sacd_sync(sacd_ctx* ctx);
+
+/*
+ * Per-kernel timing. While enabled, mode steps and fits are launched one kernel at a time (no
+ * CUDA graph) with a CUDA event pair around each kernel, on the context's stream.
+ * sacd_profile_read waits, then fills up to `cap` entries (kernel class, launches, total ms)
+ * and returns the number of classes in *n. Timing pairs beyond 65536 per enable are dropped.
+ */
+typedef struct {
+  char name[24];
+  int64_t launches;
+  double total_ms;
+} sacd_kernel_stat;
+
+sacd_status sacd_profile_enable(sacd_ctx* ctx, int32_t on);
+sacd_status sacd_profile_read(sacd_ctx* ctx, sacd_kernel_stat* out, int32_t cap, int32_t* n);
+
+/* sacd_destroy -- release everything the context owns. NULL-safe; legal on a poisoned context. */
+void sacd_destroy(sacd_ctx* ctx);
+
+/* sacd_last_error -- message of the last failed call on this thread ("" if none). */
+const char* sacd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SACD_H */

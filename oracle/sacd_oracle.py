@@ -15,7 +15,8 @@ design notes of the repository):
 
 * The delta in the importance (Eq. 20) is the projected delta of Eq. 12,
   s = max(0, u - g/h) - u, not the raw ratio of Eq. 11.
-* L is the Frobenius norm of H (symbol table; proof of Lemma 1); the spectral norm is a flag.
+* L is the Frobenius norm of H (symbol table; proof of Lemma 1); the spectral norm is a flag,
+  and "gcd" replaces L by h_rr per column (the GCD importance of Eq. 18).
 * Selection uses z from the gradient at the start of the mode step, for every element; the ti
   comparison is strict (ti^k > ti^{k-1} takes Eq. 27) and an element is updated only if sp > 0
   (strict); z^{k-1} is refreshed for every element, selected or not.
@@ -311,11 +312,14 @@ class SaCDOracle:
         A = self.A[n]
         M = mttkrp(self.dims, self.idx, self.vals, self.A, n)  # Eq. 9, X_(n)(KRP)
         H = hadamard_of_grams(self.A, n)  # Eq. 10
-        L = lipschitz(H, self.lnorm)  # Algorithm 1: L = ||H||
         G = gradient(A, H, M)  # Eq. 9 / 14
         h = np.diag(H)[None, :]
+        if self.lnorm == "gcd":
+            L = h  # Eq. 18: h_rr in place of L
+        else:
+            L = lipschitz(H, self.lnorm)  # Algorithm 1: L = ||H||
         S = projected_delta(A, G, h)  # Eq. 11-12
-        Z = importance(G, S, L)  # Eq. 20
+        Z = importance(G, S, L)  # Eq. 20 (Eq. 18 with "gcd")
         ti = total_importance(Z)  # Eq. 25
         branch = None
         if mask is None:

@@ -1,0 +1,69 @@
+// Host-side launchers of the libsacd kernels (all enqueue on the given stream, no sync).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+struct StepDesc;
+struct FitDesc;
+
+namespace sacd {
+
+// ---- MTTKRP (mttkrp.cu)
+void launch_mttkrp(const StepDesc* d_descs, const int64_t* d_tile_base, int njobs, int64_t total_tiles, int prec,
+                   int rv, cudaStream_t st);
+void launch_fixup_light(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st);
+void launch_fixup_heavy(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st);
+
+// ---- update path (update.cu)
+void configure_kernels();  // one-time kernel attributes (large dynamic shared memory)
+int rows_per_block_pass1(int Rp);
+int rows_per_block_pass2(int Rp);
+__host__ __device__ int gram_chunk_rows(int Rp);
+void launch_hl(const StepDesc* d_descs, int njobs, cudaStream_t st);
+void launch_pass1(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+                  cudaStream_t st);
+void launch_pass2(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+                  cudaStream_t st);
+void launch_gram(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+                 cudaStream_t st);
+int gram_reduce_blocks(int Rp);
+void launch_gram_reduce(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks,
+                        cudaStream_t st);
+void launch_fit(const FitDesc* d_fit, int64_t blocks, cudaStream_t st);
+void launch_to_bf16(const float* src, void* dst, int64_t n, cudaStream_t st);
+void launch_check_factor(const float* A, int64_t rows, int R, int Rp, unsigned int* bad, cudaStream_t st);
+
+// ---- preprocessing (prep.cu)
+struct SortWord {
+  int nfields;
+  int mode[8];
+  int shift[8];
+};
+// Exclusive scan of n uint32 values (out may alias in); total written to *d_total if non-null.
+void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* d_total, void* tmp, cudaStream_t st);
+size_t scan_tmp_bytes(int64_t n);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits; returns 0 if the result is
+// in (keys, vals), 1 if in (keys_alt, vals_alt).
+int radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n, int bits,
+                     void* tmp, cudaStream_t st);
+size_t radix_tmp_bytes(int64_t n);
+void launch_iota(uint32_t* p, int64_t n, cudaStream_t st);
+void launch_build_keys(const int32_t* idx, int64_t stride, const uint32_t* perm, int64_t n, SortWord w,
+                       uint64_t* keys, cudaStream_t st);
+void launch_gather_i32(const int32_t* src, const uint32_t* perm, int32_t* dst, int64_t n, cudaStream_t st);
+void launch_gather_f32(const float* src, const uint32_t* perm, float* dst, int64_t n, cudaStream_t st);
+void launch_validate_idx(const int32_t* idx, int64_t stride, int N, const int64_t* d_dims, int64_t n,
+                         unsigned int* bad, cudaStream_t st);
+void launch_dup_heads(const int32_t* sidx, int64_t stride, int N, int64_t n, uint32_t* heads, cudaStream_t st);
+void launch_dup_compact(const int32_t* sidx, int64_t stride, int N, const float* svals, const uint32_t* heads,
+                        const uint32_t* pos, int64_t n, int32_t* uidx, int64_t ustride, float* uvals,
+                        cudaStream_t st);
+void launch_sumsq(const float* v, int64_t n, double* part, int64_t nparts, double* out, unsigned int* counter,
+                  cudaStream_t st);
+void launch_split_flags(const int32_t* rowid, int64_t nnz, int64_t tile, int64_t ntiles, uint32_t* flags,
+                        cudaStream_t st);
+void launch_split_emit(const int32_t* rowid, int64_t nnz, int64_t tile, int64_t ntiles, const uint32_t* flags,
+                       const uint32_t* pos, int4* out, cudaStream_t st);
+
+}  // namespace sacd

@@ -1,0 +1,392 @@
+// Sparse MTTKRP M = X_(n) (Khatri-Rao of A_k, k != n)   (Eq. 9, first term; the slice form
+// m_r = sum over Omega^(n)_q of x * prod_k a_k[i_k, r] of Sec. 4.4, all r at once).
+//
+// Layout: the nonzeros of mode n are sorted by row i_n (slice structure built at create time).
+// They are cut into warp tiles of a fixed number of nonzeros (load balance does not depend on
+// the row-length skew). Inside a warp, lane groups of LPR lanes each own one gathered factor
+// row (LPR 16-byte vectors, 128-bit loads) and walk a contiguous sub-range of the tile,
+// accumulating in FP32 registers. A row that lies wholly inside a sub-range is stored at once.
+// Segments cut by a sub-range border are merged inside the warp (shared memory, fixed order);
+// segments cut by a tile border become per-tile partials ("carries") that a fix-up kernel sums
+// in a fixed order over a static list of split rows. No floating-point atomics: the result is
+// bitwise reproducible for a given tiling.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sacd {
+
+template <int PREC>
+struct GatherVec;
+
+template <>
+struct GatherVec<0> {  // FP32 rows: 4 columns per 16-byte vector
+  static constexpr int W = 4;
+  __device__ __forceinline__ static void load(const void* base, int64_t vec, float* out) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(base) + vec);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+  }
+};
+
+template <>
+struct GatherVec<1> {  // BF16 rows: 8 columns per 16-byte vector
+  static constexpr int W = 8;
+  __device__ __forceinline__ static void load(const void* base, int64_t vec, float* out) {
+    uint4 v = __ldg(reinterpret_cast<const uint4*>(base) + vec);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      out[2 * i] = __uint_as_float(w[i] << 16);
+      out[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+  }
+};
+
+// Per-warp scratch for the in-warp merge of open segments.
+struct WarpPieces {
+  float acc[2][256];     // [head/tail][group * Rp + column]; G * Rp <= 256 for every shape used
+  int32_t row[2][32];
+  int32_t flags[32];     // bit0 head valid (left-open), bit1 head also right-open, bit2 tail valid
+};
+
+constexpr int kWarpsPerBlock = 8;
+constexpr int kUnroll = 4;
+
+template <int PREC, int RV>
+struct TileShape {
+  static constexpr int W = GatherVec<PREC>::W;
+  static constexpr int LPR = RV < 32 ? RV : 32;  // lanes per row
+  static constexpr int CPL = RV / LPR;           // vectors per lane
+  static constexpr int G = 32 / LPR;             // lane groups per warp
+  static constexpr int NV = CPL * W;             // floats per lane
+};
+
+template <int NV>
+__device__ __forceinline__ void store_row_chunk(float* Mrow, int col0, const float* v) {
+  // col0 is a multiple of 4; NV is 4 or 8
+#pragma unroll
+  for (int i = 0; i < NV; i += 4)
+    *reinterpret_cast<float4*>(Mrow + col0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+}
+
+template <int PREC, int RV>
+__device__ __forceinline__ void lane_cols(int lig, int k, int& col0) {
+  // column of the k-th vector owned by lane `lig` of its group
+  col0 = (lig + k * TileShape<PREC, RV>::LPR) * GatherVec<PREC>::W;
+}
+
+template <int PREC, int RV>
+__device__ void zero_rows(float* __restrict__ Mout, int Rp, int64_t r0, int64_t r1, int lig) {
+  using S = TileShape<PREC, RV>;
+  float z[S::W];
+#pragma unroll
+  for (int i = 0; i < S::W; ++i) z[i] = 0.f;
+  for (int64_t r = r0; r < r1; ++r) {
+    float* Mrow = Mout + r * Rp;
+#pragma unroll
+    for (int k = 0; k < S::CPL; ++k) {
+      int c0;
+      lane_cols<PREC, RV>(lig, k, c0);
+      store_row_chunk<S::W>(Mrow, c0, z);
+    }
+  }
+}
+
+template <int PREC, int RV>
+__device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpPieces& wp) {
+  using S = TileShape<PREC, RV>;
+  const int lane = lane_id();
+  const int g = lane / S::LPR;   // group
+  const int lig = lane % S::LPR; // lane in group
+  // descriptor fields in registers (stores below cannot alias them)
+  const int64_t nnz = dp->nnz;
+  const int tile_nnz = dp->tile, sub = dp->sub, Rp = dp->Rp;
+  const int64_t I = dp->I;
+  float* __restrict__ Mout = dp->M;
+  float* __restrict__ carry = dp->carry;
+  const int32_t* __restrict__ rowid = dp->rowid;
+  const int32_t* __restrict__ cidx = dp->cidx;
+  const float* __restrict__ val = dp->val;
+  const int nother = dp->nother;
+  const void* fac[SACD_MAXN - 1];
+#pragma unroll
+  for (int m = 0; m < SACD_MAXN - 1; ++m) fac[m] = dp->fac[m];
+  const int64_t t0 = tile * tile_nnz;
+  const int64_t t1 = min(t0 + (int64_t)tile_nnz, nnz);
+  const int64_t a = t0 + (int64_t)g * sub;
+  const int64_t b = min(a + (int64_t)sub, t1);
+  const int rv = RV;
+
+  float acc[S::NV];
+#pragma unroll
+  for (int i = 0; i < S::NV; ++i) acc[i] = 0.f;
+  int32_t cur = -1;
+  int64_t seg = a;
+  int flags = 0;
+  const int32_t before = (a > 0 && a < b) ? __ldg(rowid + a - 1) : -1;
+  const int32_t after = (b < nnz && a < b) ? __ldg(rowid + b) : -1;
+
+  // close the segment [s, e_end) of row `row`
+  auto close_seg = [&](int32_t row, int64_t s, int64_t e_end) {
+    const bool lopen = (s == a) && (before == row);
+    const bool ropen = (e_end == b) && (after == row);
+    if (!lopen && !ropen) {
+      float* Mrow = Mout + (int64_t)row * Rp;
+#pragma unroll
+      for (int k = 0; k < S::CPL; ++k) {
+        int c0;
+        lane_cols<PREC, RV>(lig, k, c0);
+        store_row_chunk<S::W>(Mrow, c0, acc + k * S::W);
+      }
+    } else {
+      const int slot = lopen ? 0 : 1;
+      float* dst = &wp.acc[slot][0] + (g * Rp);
+#pragma unroll
+      for (int k = 0; k < S::CPL; ++k) {
+        int c0;
+        lane_cols<PREC, RV>(lig, k, c0);
+#pragma unroll
+        for (int i = 0; i < S::W; ++i) dst[c0 + i] = acc[k * S::W + i];
+      }
+      if (lig == 0) wp.row[slot][g] = row;
+      flags |= lopen ? (ropen ? 3 : 1) : 4;
+    }
+  };
+
+  for (int64_t e0 = a; e0 < b; e0 += kUnroll) {
+    int32_t rows[kUnroll];
+    float prod[kUnroll][S::NV];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t e = e0 + u;
+      if (e < b) {
+        rows[u] = __ldg(rowid + e);
+        const float x = __ldg(val + e);
+#pragma unroll
+        for (int i = 0; i < S::NV; ++i) prod[u][i] = x;
+#pragma unroll
+        for (int m = 0; m < SACD_MAXN - 1; ++m) {
+          if (m < nother) {
+            const int64_t r = __ldg(cidx + (int64_t)m * nnz + e);
+#pragma unroll
+            for (int k = 0; k < S::CPL; ++k) {
+              float v[S::W];
+              GatherVec<PREC>::load(fac[m], r * rv + lig + k * S::LPR, v);
+#pragma unroll
+              for (int i = 0; i < S::W; ++i) prod[u][k * S::W + i] *= v[i];
+            }
+          }
+        }
+      } else {
+        rows[u] = -1;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t e = e0 + u;
+      if (e < b) {
+        if (rows[u] != cur) {
+          if (cur >= 0) close_seg(cur, seg, e);
+          // rows strictly between the previous nonzero's row and this one are empty
+          const int32_t prev = (e == a) ? before : cur;
+          if (prev != rows[u]) zero_rows<PREC, RV>(Mout, Rp, (int64_t)prev + 1, rows[u], lig);
+          cur = rows[u];
+          seg = e;
+#pragma unroll
+          for (int i = 0; i < S::NV; ++i) acc[i] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < S::NV; ++i) acc[i] += prod[u][i];
+      }
+    }
+  }
+  if (cur >= 0) {
+    close_seg(cur, seg, b);
+    if (b == nnz) zero_rows<PREC, RV>(Mout, Rp, (int64_t)cur + 1, I, lig);
+  }
+  if (lig == 0) wp.flags[g] = flags;
+  __syncwarp();
+
+  // In-warp merge of the open pieces, groups in order, by the lanes of group 0.
+  if (g == 0) {
+    bool run_valid = false, run_tile_left = false;
+    int32_t run_row = -1;
+    float run[S::NV];
+    auto finish = [&](bool right_open_at_tile) {
+      float* dst;
+      if (run_tile_left || right_open_at_tile) {
+        const int slot = run_tile_left ? 0 : 1;
+        dst = carry + (tile * 2 + slot) * (int64_t)Rp;
+      } else {
+        dst = Mout + (int64_t)run_row * Rp;
+      }
+#pragma unroll
+      for (int k = 0; k < S::CPL; ++k) {
+        int c0;
+        lane_cols<PREC, RV>(lig, k, c0);
+        store_row_chunk<S::W>(dst, c0, run + k * S::W);
+      }
+    };
+    for (int gg = 0; gg < S::G; ++gg) {
+      const int f = wp.flags[gg];
+      if (f & 1) {
+        const float* src = &wp.acc[0][0] + gg * Rp;
+        if (!run_valid) {
+          run_valid = true;
+          run_tile_left = true;  // only possible for the tile's first group
+          run_row = wp.row[0][gg];
+#pragma unroll
+          for (int k = 0; k < S::CPL; ++k) {
+            int c0;
+            lane_cols<PREC, RV>(lig, k, c0);
+#pragma unroll
+            for (int i = 0; i < S::W; ++i) run[k * S::W + i] = src[c0 + i];
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < S::CPL; ++k) {
+            int c0;
+            lane_cols<PREC, RV>(lig, k, c0);
+#pragma unroll
+            for (int i = 0; i < S::W; ++i) run[k * S::W + i] += src[c0 + i];
+          }
+        }
+        if (!(f & 2)) {
+          finish(false);
+          run_valid = false;
+        }
+      }
+      if (f & 4) {
+        const float* src = &wp.acc[1][0] + gg * Rp;
+        run_valid = true;
+        run_tile_left = false;
+        run_row = wp.row[1][gg];
+#pragma unroll
+        for (int k = 0; k < S::CPL; ++k) {
+          int c0;
+          lane_cols<PREC, RV>(lig, k, c0);
+#pragma unroll
+          for (int i = 0; i < S::W; ++i) run[k * S::W + i] = src[c0 + i];
+        }
+      }
+    }
+    if (run_valid) finish(true);
+  }
+}
+
+template <int PREC, int RV>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    mttkrp_kernel(const StepDesc* __restrict__ descs, const int64_t* __restrict__ tile_base, int njobs,
+                  int64_t total_tiles) {
+  __shared__ WarpPieces pieces[kWarpsPerBlock];
+  const int warp = threadIdx.x >> 5;
+  const int64_t gt = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (gt >= total_tiles) return;
+  const int j = njobs > 1 ? find_job(tile_base, njobs, gt) : 0;
+  mttkrp_tile<PREC, RV>(descs + j, gt - tile_base[j], pieces[warp]);
+}
+
+// Rows split across tiles, with few partials: one warp per row, partials summed in tile order.
+__global__ void __launch_bounds__(256)
+    fixup_light_kernel(const StepDesc* __restrict__ descs, const int64_t* __restrict__ item_base, int njobs,
+                       int64_t total) {
+  const int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gi >= total) return;
+  const int j = njobs > 1 ? find_job(item_base, njobs, gi) : 0;
+  const StepDesc& d = descs[j];
+  const int4 s = d.split_light[gi - item_base[j]];
+  const int nvec = d.Rp >> 2;
+  const float4* carry = reinterpret_cast<const float4*>(d.carry);
+  float4* Mrow = reinterpret_cast<float4*>(d.M + (int64_t)s.x * d.Rp);
+  for (int c = lane_id(); c < nvec; c += 32) {
+    float4 acc = carry[((int64_t)s.y * 2 + 1) * nvec + c];
+    for (int64_t t = s.y + 1; t <= s.z; ++t) {
+      const float4 v = carry[(t * 2) * nvec + c];
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    Mrow[c] = acc;
+  }
+}
+
+// Rows split across many tiles: one block per row; threads take partials strided, then a
+// fixed-shape tree in shared memory.
+__global__ void __launch_bounds__(256)
+    fixup_heavy_kernel(const StepDesc* __restrict__ descs, const int64_t* __restrict__ item_base, int njobs,
+                       int64_t total) {
+  __shared__ float4 red[256];
+  const int64_t gi = blockIdx.x;
+  if (gi >= total) return;
+  const int j = njobs > 1 ? find_job(item_base, njobs, gi) : 0;
+  const StepDesc& d = descs[j];
+  const int4 s = d.split_heavy[gi - item_base[j]];
+  const int nvec = d.Rp >> 2;
+  const float4* carry = reinterpret_cast<const float4*>(d.carry);
+  float4* Mrow = reinterpret_cast<float4*>(d.M + (int64_t)s.x * d.Rp);
+  const int64_t P = (int64_t)s.z - s.y + 1;  // partials: slot 1 of tile s.y, slot 0 of the rest
+  for (int c0 = 0; c0 < nvec; c0 += 256) {
+    const int cw = min(256, nvec - c0);      // vectors handled in this pass
+    const int lanes = 256 / cw;              // partial lanes (cw divides 256: powers of two)
+    const int c = c0 + (threadIdx.x % cw);
+    const int pl = threadIdx.x / cw;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pl < lanes) {
+      for (int64_t p = pl; p < P; p += lanes) {
+        const int64_t t = s.y + p;
+        const float4 v = carry[(t * 2 + (p == 0 ? 1 : 0)) * nvec + c];
+        acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+      }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = lanes >> 1; w >= 1; w >>= 1) {
+      if (pl < w) {
+        const float4 o = red[threadIdx.x + w * cw];
+        float4 m = red[threadIdx.x];
+        m.x += o.x; m.y += o.y; m.z += o.z; m.w += o.w;
+        red[threadIdx.x] = m;
+      }
+      __syncthreads();
+    }
+    if (pl == 0) Mrow[c] = red[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+template <int PREC>
+static void launch_mttkrp_prec(const StepDesc* d_descs, const int64_t* d_tile_base, int njobs, int64_t total_tiles,
+                               int rv, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((total_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  const int T = kWarpsPerBlock * 32;
+  switch (rv) {
+    case 1: mttkrp_kernel<PREC, 1><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 2: mttkrp_kernel<PREC, 2><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 4: mttkrp_kernel<PREC, 4><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 8: mttkrp_kernel<PREC, 8><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 16: mttkrp_kernel<PREC, 16><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 32: mttkrp_kernel<PREC, 32><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 64: mttkrp_kernel<PREC, 64><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    default: break;
+  }
+}
+
+// All jobs of one launch share the gathered-row width `rv` (16-byte vectors per row).
+void launch_mttkrp(const StepDesc* d_descs, const int64_t* d_tile_base, int njobs, int64_t total_tiles, int prec,
+                   int rv, cudaStream_t st) {
+  if (total_tiles <= 0) return;
+  if (prec == 0)
+    launch_mttkrp_prec<0>(d_descs, d_tile_base, njobs, total_tiles, rv, st);
+  else
+    launch_mttkrp_prec<1>(d_descs, d_tile_base, njobs, total_tiles, rv, st);
+}
+
+void launch_fixup_light(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st) {
+  if (total <= 0) return;
+  const int64_t blocks = (total * 32 + 255) / 256;
+  fixup_light_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_descs, d_base, njobs, total);
+}
+
+void launch_fixup_heavy(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st) {
+  if (total <= 0) return;
+  fixup_heavy_kernel<<<(unsigned)total, 256, 0, st>>>(d_descs, d_base, njobs, total);
+}
+
+}  // namespace sacd

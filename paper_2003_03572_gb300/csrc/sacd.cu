@@ -1,0 +1,998 @@
+// Host side of libsacd: the C ABI declared in include/sacd.h.
+//
+// A context owns one sparse tensor (per-mode sorted slice structures), the FP32 master factors
+// (plus BF16 mirrors in the BF16-gather mode), z^{k-1}, the FP64 Grams and the per-mode scalar
+// state of Algorithm 1 (ti^{k-1}, first visit). Every mode step is a fixed sequence of kernels
+// on the context's stream; sacd_iterate captures one outer iteration (modes 0..N-1) in a CUDA
+// graph and replays it, so that no host round trip happens between mode steps.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sacd.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace sacd;
+
+namespace {
+
+thread_local std::string g_err;
+
+sacd_status fail(sacd_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+enum KClass { K_HL = 0, K_MTTKRP, K_FIXUP, K_PASS1, K_PASS2, K_GRAM, K_FIT, K_NCLASS };
+const char* kClassName[K_NCLASS] = {"hl", "mttkrp", "mttkrp_fixup", "pass1_grad_importance",
+                                    "pass2_select_update", "gram", "fit"};
+
+struct ModeData {
+  int64_t I = 0;
+  // slice structure
+  int32_t* rowid = nullptr;
+  int32_t* cidx = nullptr;
+  float* val = nullptr;
+  int64_t ntiles = 0;
+  int sub = 0, tile = 0;
+  int4* split_light = nullptr;
+  int64_t nlight = 0;
+  int4* split_heavy = nullptr;
+  int64_t nheavy = 0;
+  // state
+  float* A = nullptr;
+  __nv_bfloat16* A16 = nullptr;
+  float* zprev = nullptr;
+  float* M = nullptr;
+  double* gram = nullptr;
+  int64_t p1_blocks = 0, p2_blocks = 0, gram_blocks = 0;
+};
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // pairs
+  std::vector<int> cls;         // class of each used pair
+  int used = 0;
+  int64_t launches[K_NCLASS] = {0};
+  double ms[K_NCLASS] = {0};
+  int64_t dropped = 0;
+};
+
+}  // namespace
+
+struct sacd_ctx {
+  int N = 0;
+  int64_t dims[SACD_MAXN] = {0};
+  int64_t nnz = 0;
+  int R = 0, Rp = 0, rv = 0;
+  int prec = 0, lnorm = 0, fixup = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  bool poisoned = false;
+  bool debug = false;
+  int last_mode = -1;
+  bool mlast_valid = false;
+  int replay_mode = -1;
+  double norm_x_sq = 0.0;
+  int64_t device_bytes = 0;
+  std::vector<void*> allocs;
+  ModeData m[SACD_MAXN];
+  // shared scratch
+  float* G = nullptr;
+  uint8_t* mask = nullptr;
+  uint8_t* replay = nullptr;
+  float* carry = nullptr;
+  double* gpart = nullptr;
+  double* H = nullptr;
+  float* Hf = nullptr;
+  float* invh = nullptr;
+  float* lh = nullptr;
+  double* tipart = nullptr;
+  double* state = nullptr;
+  unsigned int* counters = nullptr;
+  unsigned long long* nsel = nullptr;
+  int64_t* zero64 = nullptr;
+  StepDesc hdesc[SACD_MAXN];
+  StepDesc* ddesc = nullptr;
+  FitDesc hfit;
+  FitDesc* dfit = nullptr;
+  double* fitpart = nullptr;
+  double* fitout = nullptr;
+  int64_t fit_blocks = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  Prof prof;
+};
+
+namespace {
+
+sacd_status cuda_fail(sacd_ctx* c, cudaError_t e, const char* where) {
+  if (c) c->poisoned = true;
+  return fail(SACD_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr)                                              \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, #expr);    \
+  } while (0)
+
+template <typename T>
+sacd_status dalloc(sacd_ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  const cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SACD_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+  }
+  c->allocs.push_back(q);
+  c->device_bytes += (int64_t)(count * sizeof(T));
+  *p = reinterpret_cast<T*>(q);
+  return SACD_OK;
+}
+
+#define TRY(expr)                        \
+  do {                                   \
+    sacd_status _s = (expr);             \
+    if (_s != SACD_OK) return _s;        \
+  } while (0)
+
+// temporaries that are freed at the end of sacd_create
+struct TmpAllocs {
+  std::vector<void*> p;
+  ~TmpAllocs() {
+    for (void* q : p) cudaFree(q);
+  }
+  template <typename T>
+  sacd_status get(T** out, size_t count) {
+    *out = nullptr;
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SACD_ENOMEM, "cudaMalloc of temporary " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    p.push_back(q);
+    *out = reinterpret_cast<T*>(q);
+    return SACD_OK;
+  }
+};
+
+int bits_for(int64_t dim) {
+  int b = 0;
+  while (b < 63 && ((int64_t)1 << b) < dim) ++b;
+  return b;  // dim <= 2^b, indices < 2^b
+}
+
+int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+void prof_record(sacd_ctx* c, int cls, bool start) {
+  Prof& p = c->prof;
+  if (!p.on) return;
+  if (start) {
+    if (p.used * 2 + 2 > (int)p.ev.size()) {  // pool full: harvest
+      cudaStreamSynchronize(c->st);
+      for (int i = 0; i < p.used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]) == cudaSuccess) {
+          p.ms[p.cls[i]] += ms;
+          p.launches[p.cls[i]] += 1;
+        } else {
+          cudaGetLastError();
+          p.dropped++;
+        }
+      }
+      p.used = 0;
+    }
+    p.cls[p.used] = cls;
+    cudaEventRecord(p.ev[2 * p.used], c->st);
+  } else {
+    cudaEventRecord(p.ev[2 * p.used + 1], c->st);
+    p.used++;
+  }
+}
+
+struct KScope {
+  sacd_ctx* c;
+  int cls;
+  KScope(sacd_ctx* c_, int cls_) : c(c_), cls(cls_) { prof_record(c, cls, true); }
+  ~KScope() { prof_record(c, cls, false); }
+};
+
+void enqueue_mttkrp(sacd_ctx* c, int n) {
+  ModeData& md = c->m[n];
+  StepDesc* dd = c->ddesc + n;
+  if (c->nnz == 0) {
+    cudaMemsetAsync(md.M, 0, (size_t)md.I * c->Rp * sizeof(float), c->st);
+    return;
+  }
+  {
+    KScope k(c, K_MTTKRP);
+    launch_mttkrp(dd, c->zero64, 1, md.ntiles, c->prec, c->rv, c->st);
+  }
+  if (md.nlight) {
+    KScope k(c, K_FIXUP);
+    launch_fixup_light(dd, c->zero64, 1, md.nlight, c->st);
+  }
+  if (md.nheavy) {
+    KScope k(c, K_FIXUP);
+    launch_fixup_heavy(dd, c->zero64, 1, md.nheavy, c->st);
+  }
+}
+
+void enqueue_gram(sacd_ctx* c, int n) {
+  KScope k(c, K_GRAM);
+  launch_gram(c->ddesc + n, c->zero64, 1, c->m[n].gram_blocks, c->Rp, c->st);
+  launch_gram_reduce(c->ddesc + n, c->zero64, 1, gram_reduce_blocks(c->Rp), c->st);
+}
+
+void enqueue_step(sacd_ctx* c, int n) {
+  ModeData& md = c->m[n];
+  StepDesc* dd = c->ddesc + n;
+  {
+    KScope k(c, K_HL);
+    launch_hl(dd, 1, c->st);
+  }
+  enqueue_mttkrp(c, n);
+  {
+    KScope k(c, K_PASS1);
+    launch_pass1(dd, c->zero64, 1, md.p1_blocks, c->Rp, c->st);
+  }
+  {
+    KScope k(c, K_PASS2);
+    launch_pass2(dd, c->zero64, 1, md.p2_blocks, c->Rp, c->st);
+  }
+  enqueue_gram(c, n);
+}
+
+void invalidate_graph(sacd_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+}
+
+sacd_status upload_descs(sacd_ctx* c) {
+  for (int n = 0; n < c->N; ++n) c->hdesc[n].mask = c->debug ? c->mask : nullptr;
+  CK(cudaMemcpyAsync(c->ddesc, c->hdesc, sizeof(StepDesc) * c->N, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  invalidate_graph(c);
+  return SACD_OK;
+}
+
+sacd_status check_ctx(sacd_ctx* c) {
+  if (!c) return fail(SACD_EINVAL, "null context");
+  if (c->poisoned) return fail(SACD_ESTATE, "context is poisoned by an earlier CUDA error");
+  return SACD_OK;
+}
+
+struct SortBufs {
+  uint64_t *k0 = nullptr, *k1 = nullptr;
+  uint32_t *p0 = nullptr, *p1 = nullptr;
+  char* tmp = nullptr;
+  sacd_status alloc(TmpAllocs& T, int64_t n) {
+    TRY(T.get(&k0, n));
+    TRY(T.get(&k1, n));
+    TRY(T.get(&p0, n));
+    TRY(T.get(&p1, n));
+    TRY(T.get(&tmp, radix_tmp_bytes(n)));
+    return SACD_OK;
+  }
+};
+
+// Sort permutation of n coordinates (SoA idx with row stride `stride`) in the lexicographic
+// order of the modes listed in `order` (most significant first).
+sacd_status sort_order(sacd_ctx* c, SortBufs& B, const int32_t* idx, int64_t stride, int64_t n,
+                       const std::vector<int>& order, uint32_t** perm_out) {
+  uint64_t* k0 = B.k0;
+  uint64_t* k1 = B.k1;
+  uint32_t* p0 = B.p0;
+  uint32_t* p1 = B.p1;
+  void* tmp = B.tmp;
+  launch_iota(p0, n, c->st);
+  // pack words from the least significant mode upward
+  std::vector<SortWord> words;
+  SortWord cur{};
+  int cur_bits = 0;
+  for (int i = (int)order.size() - 1; i >= 0; --i) {
+    const int md = order[i];
+    const int b = bits_for(c->dims[md]);
+    if (b == 0) continue;
+    if (cur_bits + b > 64) {
+      words.push_back(cur);
+      cur = SortWord{};
+      cur_bits = 0;
+    }
+    cur.mode[cur.nfields] = md;
+    cur.shift[cur.nfields] = cur_bits;
+    cur.nfields++;
+    cur_bits += b;
+  }
+  if (cur.nfields) words.push_back(cur);
+  uint32_t* perm = p0;
+  uint32_t* alt = p1;
+  for (const SortWord& w : words) {
+    int wbits = 0;
+    for (int f = 0; f < w.nfields; ++f) wbits = std::max(wbits, w.shift[f] + bits_for(c->dims[w.mode[f]]));
+    launch_build_keys(idx, stride, perm, n, w, k0, c->st);
+    const int which = radix_sort_pairs(k0, perm, k1, alt, n, wbits, tmp, c->st);
+    if (which == 1) std::swap(perm, alt);
+  }
+  CK(cudaGetLastError());
+  *perm_out = perm;
+  return SACD_OK;
+}
+
+sacd_status build_mode(sacd_ctx* c, TmpAllocs& T, SortBufs& B, int n, const int32_t* uidx, const float* uvals) {
+  ModeData& md = c->m[n];
+  const int64_t nnz = c->nnz;
+  const int N = c->N;
+  TRY(dalloc(c, &md.rowid, nnz));
+  TRY(dalloc(c, &md.cidx, (size_t)(N - 1) * nnz));
+  TRY(dalloc(c, &md.val, nnz));
+  std::vector<int> order;
+  order.push_back(n);
+  for (int k = 0; k < N; ++k)
+    if (k != n) order.push_back(k);
+  if (nnz > 0) {
+    uint32_t* perm = nullptr;
+    TRY(sort_order(c, B, uidx, nnz, nnz, order, &perm));
+    launch_gather_i32(uidx + (int64_t)n * nnz, perm, md.rowid, nnz, c->st);
+    int o = 0;
+    for (int k = 0; k < N; ++k)
+      if (k != n) launch_gather_i32(uidx + (int64_t)k * nnz, perm, md.cidx + (int64_t)(o++) * nnz, nnz, c->st);
+    launch_gather_f32(uvals, perm, md.val, nnz, c->st);
+    CK(cudaGetLastError());
+  }
+  // warp tiles
+  const int lpr = std::min(c->rv, 32);
+  const int groups = 32 / lpr;
+  int64_t sub = nnz / ((int64_t)groups * 152 * 64);
+  sub = std::max<int64_t>(8, std::min<int64_t>(128, sub));
+  sub = (sub + 3) / 4 * 4;
+  md.sub = (int)sub;
+  md.tile = (int)(groups * sub);
+  md.ntiles = (nnz + md.tile - 1) / md.tile;
+  // rows split across tiles
+  md.nlight = md.nheavy = 0;
+  if (md.ntiles > 1) {
+    uint32_t *flags, *pos, *tot;
+    void* stmp;
+    int4* lst;
+    TRY(T.get(&flags, md.ntiles));
+    TRY(T.get(&pos, md.ntiles));
+    TRY(T.get(&tot, 1));
+    TRY(T.get(reinterpret_cast<char**>(&stmp), scan_tmp_bytes(md.ntiles)));  // NOLINT
+    launch_split_flags(md.rowid, nnz, md.tile, md.ntiles, flags, c->st);
+    scan_u32(flags, pos, md.ntiles, tot, stmp, c->st);
+    uint32_t h_tot = 0;
+    CK(cudaMemcpyAsync(&h_tot, tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (h_tot) {
+      TRY(T.get(&lst, h_tot));
+      launch_split_emit(md.rowid, nnz, md.tile, md.ntiles, flags, pos, lst, c->st);
+      std::vector<int4> h(h_tot);
+      CK(cudaMemcpyAsync(h.data(), lst, sizeof(int4) * h_tot, cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      std::vector<int4> light, heavy;
+      for (const int4& s : h) ((s.z - s.y + 1) <= 16 ? light : heavy).push_back(s);
+      md.nlight = (int64_t)light.size();
+      md.nheavy = (int64_t)heavy.size();
+      TRY(dalloc(c, &md.split_light, light.size()));
+      TRY(dalloc(c, &md.split_heavy, heavy.size()));
+      if (!light.empty())
+        CK(cudaMemcpyAsync(md.split_light, light.data(), sizeof(int4) * light.size(), cudaMemcpyHostToDevice,
+                           c->st));
+      if (!heavy.empty())
+        CK(cudaMemcpyAsync(md.split_heavy, heavy.data(), sizeof(int4) * heavy.size(), cudaMemcpyHostToDevice,
+                           c->st));
+      CK(cudaStreamSynchronize(c->st));
+    }
+  }
+  return SACD_OK;
+}
+
+sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
+  *out = nullptr;
+  if (!cfg) return fail(SACD_EINVAL, "null config");
+  const int N = cfg->nmodes;
+  if (N < 2 || N > SACD_MAXN) return fail(SACD_EINVAL, "nmodes must be in [2, 8]");
+  if (!cfg->dims) return fail(SACD_EINVAL, "null dims");
+  for (int n = 0; n < N; ++n)
+    if (cfg->dims[n] < 1 || cfg->dims[n] > 2147483647LL) return fail(SACD_EINVAL, "dims[n] must be in [1, 2^31-1]");
+  if (cfg->nnz < 0 || cfg->nnz > 2147483647LL) return fail(SACD_EINVAL, "nnz must be in [0, 2^31-1]");
+  if (cfg->rank < 1 || cfg->rank > SACD_MAXR) return fail(SACD_EINVAL, "rank must be in [1, 256]");
+  if (cfg->precision != SACD_FP32 && cfg->precision != SACD_BF16_GATHER) return fail(SACD_EINVAL, "bad precision");
+  if (cfg->lnorm < 0 || cfg->lnorm > 2) return fail(SACD_EINVAL, "bad lnorm");
+  if (cfg->fixup < 0 || cfg->fixup > 1) return fail(SACD_EINVAL, "bad fixup");
+  if (cfg->nnz > 0 && (!cfg->idx || !cfg->vals)) return fail(SACD_EINVAL, "null idx or vals");
+  if (cfg->nnz > 0)
+    for (int n = 0; n < N; ++n)
+      if (!cfg->idx[n]) return fail(SACD_EINVAL, "null idx[n]");
+  if (cfg->init)
+    for (int n = 0; n < N; ++n)
+      if (!cfg->init[n]) return fail(SACD_EINVAL, "null init[n]");
+
+  sacd_ctx* c = new (std::nothrow) sacd_ctx();
+  if (!c) return fail(SACD_ENOMEM, "host allocation failed");
+  struct Guard {
+    sacd_ctx*& c;
+    bool ok = false;
+    ~Guard() {
+      if (!ok && c) sacd_destroy(c);
+    }
+  } guard{c};
+
+  c->N = N;
+  for (int n = 0; n < N; ++n) c->dims[n] = cfg->dims[n];
+  c->R = cfg->rank;
+  c->Rp = std::max(8, next_pow2(c->R));
+  c->prec = cfg->precision;
+  c->rv = c->prec == SACD_FP32 ? c->Rp / 4 : c->Rp / 8;
+  c->lnorm = cfg->lnorm;
+  c->fixup = cfg->fixup;
+  configure_kernels();
+  if (cfg->stream) {
+    c->st = reinterpret_cast<cudaStream_t>(cfg->stream);
+  } else {
+    CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  const int R = c->R, Rp = c->Rp;
+  const cudaMemcpyKind in_kind = cfg->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+
+  // ---- small shared state
+  TRY(dalloc(c, &c->zero64, 1));
+  CK(cudaMemsetAsync(c->zero64, 0, sizeof(int64_t), c->st));
+  TRY(dalloc(c, &c->state, (size_t)N * ST_STRIDE));
+  {
+    std::vector<double> st0((size_t)N * ST_STRIDE, 0.0);
+    for (int n = 0; n < N; ++n) st0[(size_t)n * ST_STRIDE + ST_FIRST] = 1.0;
+    CK(cudaMemcpyAsync(c->state, st0.data(), sizeof(double) * st0.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
+  TRY(dalloc(c, &c->counters, 8));
+  CK(cudaMemsetAsync(c->counters, 0, 8 * sizeof(unsigned int), c->st));
+  TRY(dalloc(c, &c->nsel, N));
+  CK(cudaMemsetAsync(c->nsel, 0, N * sizeof(unsigned long long), c->st));
+  int64_t* d_dims;
+  TRY(dalloc(c, &d_dims, N));
+  CK(cudaMemcpyAsync(d_dims, c->dims, sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->st));
+
+  TmpAllocs T;
+  SortBufs B;
+  const int64_t nnz_in = cfg->nnz;
+  TRY(B.alloc(T, std::max<int64_t>(nnz_in, 1)));
+  int32_t* uidx = nullptr;
+  float* uvals = nullptr;
+  {
+    // ---- COO in, validated, sorted (mode 0 order), repeats summed
+    int32_t* idx_in;
+    float* vals_in;
+    unsigned int* bad;
+    TRY(T.get(&idx_in, (size_t)N * std::max<int64_t>(nnz_in, 1)));
+    TRY(T.get(&vals_in, std::max<int64_t>(nnz_in, 1)));
+    TRY(T.get(&bad, 1));
+    CK(cudaMemsetAsync(bad, 0, sizeof(unsigned int), c->st));
+    if (nnz_in > 0) {
+      for (int n = 0; n < N; ++n)
+        CK(cudaMemcpyAsync(idx_in + (int64_t)n * nnz_in, cfg->idx[n], sizeof(int32_t) * nnz_in, in_kind, c->st));
+      CK(cudaMemcpyAsync(vals_in, cfg->vals, sizeof(float) * nnz_in, in_kind, c->st));
+      launch_validate_idx(idx_in, nnz_in, N, d_dims, nnz_in, bad, c->st);
+    }
+    unsigned int h_bad = 0;
+    CK(cudaMemcpyAsync(&h_bad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (h_bad) return fail(SACD_EINVAL, "a coordinate is outside [0, dims[n])");
+
+    int64_t nnz = 0;
+    if (nnz_in > 0) {
+      std::vector<int> order(N);
+      for (int n = 0; n < N; ++n) order[n] = n;
+      uint32_t* perm = nullptr;
+      TRY(sort_order(c, B, idx_in, nnz_in, nnz_in, order, &perm));
+      int32_t* sidx;
+      float* svals;
+      uint32_t *heads, *pos, *tot;
+      void* stmp;
+      TRY(T.get(&sidx, (size_t)N * nnz_in));
+      TRY(T.get(&svals, nnz_in));
+      TRY(T.get(&heads, nnz_in));
+      TRY(T.get(&pos, nnz_in));
+      TRY(T.get(&tot, 1));
+      TRY(T.get(reinterpret_cast<char**>(&stmp), scan_tmp_bytes(nnz_in)));
+      for (int n = 0; n < N; ++n)
+        launch_gather_i32(idx_in + (int64_t)n * nnz_in, perm, sidx + (int64_t)n * nnz_in, nnz_in, c->st);
+      launch_gather_f32(vals_in, perm, svals, nnz_in, c->st);
+      launch_dup_heads(sidx, nnz_in, N, nnz_in, heads, c->st);
+      scan_u32(heads, pos, nnz_in, tot, stmp, c->st);
+      uint32_t h_tot = 0;
+      CK(cudaMemcpyAsync(&h_tot, tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      nnz = h_tot;
+      TRY(T.get(&uidx, (size_t)N * nnz));
+      TRY(T.get(&uvals, nnz));
+      launch_dup_compact(sidx, nnz_in, N, svals, heads, pos, nnz_in, uidx, nnz, uvals, c->st);
+      CK(cudaGetLastError());
+    }
+    c->nnz = nnz;
+  }
+  // ||X||^2
+  {
+    double *part, *outp;
+    TRY(T.get(&part, 1024));
+    TRY(T.get(&outp, 1));
+    if (c->nnz > 0) {
+      launch_sumsq(uvals, c->nnz, part, 1024, outp, c->counters + 4, c->st);
+      CK(cudaMemcpyAsync(&c->norm_x_sq, outp, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+  }
+  // ---- per-mode slice structures
+  for (int n = 0; n < N; ++n) {
+    c->m[n].I = c->dims[n];
+    TRY(build_mode(c, T, B, n, uidx, uvals));
+  }
+  // ---- factors and state
+  int64_t Imax = 0, tiles_max = 0, p1_max = 0, gb_max = 0;
+  const int RB1 = rows_per_block_pass1(Rp), RB2 = rows_per_block_pass2(Rp);
+  const int CH = gram_chunk_rows(Rp);
+  for (int n = 0; n < N; ++n) {
+    ModeData& md = c->m[n];
+    const int64_t I = md.I;
+    Imax = std::max(Imax, I);
+    tiles_max = std::max(tiles_max, md.ntiles);
+    md.p1_blocks = (I + RB1 - 1) / RB1;
+    md.p2_blocks = (I + RB2 - 1) / RB2;
+    md.gram_blocks = std::min<int64_t>((I + CH - 1) / CH, 152);
+    p1_max = std::max(p1_max, md.p1_blocks);
+    gb_max = std::max(gb_max, md.gram_blocks);
+    TRY(dalloc(c, &md.A, (size_t)I * Rp));
+    TRY(dalloc(c, &md.zprev, (size_t)I * Rp));
+    TRY(dalloc(c, &md.M, (size_t)I * Rp));
+    TRY(dalloc(c, &md.gram, (size_t)Rp * Rp));
+    if (c->prec == SACD_BF16_GATHER) TRY(dalloc(c, &md.A16, (size_t)I * Rp));
+    CK(cudaMemsetAsync(md.A, 0, sizeof(float) * I * Rp, c->st));
+    CK(cudaMemsetAsync(md.zprev, 0, sizeof(float) * I * Rp, c->st));
+    CK(cudaMemsetAsync(md.M, 0, sizeof(float) * I * Rp, c->st));
+    if (cfg->init) {
+      const cudaMemcpyKind k = cfg->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+      if (!cfg->inputs_on_device) {
+        for (int64_t e = 0; e < I * R; ++e) {
+          const float v = cfg->init[n][e];
+          if (!(v >= 0.f) || !std::isfinite(v)) return fail(SACD_EINVAL, "init values must be finite and >= 0");
+        }
+      }
+      CK(cudaMemcpy2DAsync(md.A, sizeof(float) * Rp, cfg->init[n], sizeof(float) * R, sizeof(float) * R, I, k,
+                           c->st));
+    } else {
+      std::vector<float> h((size_t)I * Rp, 0.f);
+      uint64_t s = cfg->seed ^ (0xA5A5A5A5ull * (uint64_t)(n + 1));
+      for (int64_t i = 0; i < I; ++i)
+        for (int r = 0; r < R; ++r) h[(size_t)i * Rp + r] = (float)((splitmix64(s) >> 40) * (1.0 / 16777216.0));
+      CK(cudaMemcpyAsync(md.A, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, c->st));
+      CK(cudaStreamSynchronize(c->st));
+    }
+    if (md.A16) launch_to_bf16(md.A, md.A16, I * Rp, c->st);
+  }
+  if (cfg->init && cfg->inputs_on_device) {
+    unsigned int* bad;
+    TRY(T.get(&bad, 1));
+    CK(cudaMemsetAsync(bad, 0, sizeof(unsigned int), c->st));
+    for (int n = 0; n < N; ++n) launch_check_factor(c->m[n].A, c->m[n].I, R, Rp, bad, c->st);
+    unsigned int h_bad = 0;
+    CK(cudaMemcpyAsync(&h_bad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (h_bad) return fail(SACD_EINVAL, "init values must be finite and >= 0");
+  }
+  TRY(dalloc(c, &c->G, (size_t)Imax * Rp));
+  TRY(dalloc(c, &c->mask, (size_t)Imax * Rp));
+  TRY(dalloc(c, &c->replay, (size_t)Imax * Rp));
+  TRY(dalloc(c, &c->carry, (size_t)std::max<int64_t>(tiles_max, 1) * 2 * Rp));
+  TRY(dalloc(c, &c->gpart, (size_t)gb_max * Rp * Rp));
+  TRY(dalloc(c, &c->H, (size_t)Rp * Rp));
+  TRY(dalloc(c, &c->Hf, (size_t)Rp * Rp));
+  TRY(dalloc(c, &c->invh, Rp));
+  TRY(dalloc(c, &c->lh, Rp));
+  TRY(dalloc(c, &c->tipart, p1_max));
+  CK(cudaMemsetAsync(c->G, 0, sizeof(float) * Imax * Rp, c->st));
+  CK(cudaMemsetAsync(c->mask, 0, Imax * Rp, c->st));
+  CK(cudaMemsetAsync(c->replay, 0, Imax * Rp, c->st));
+  CK(cudaMemsetAsync(c->H, 0, sizeof(double) * Rp * Rp, c->st));
+
+  // ---- step descriptors
+  TRY(dalloc(c, &c->ddesc, N));
+  for (int n = 0; n < N; ++n) {
+    ModeData& md = c->m[n];
+    StepDesc& d = c->hdesc[n];
+    memset(&d, 0, sizeof(d));
+    d.rowid = md.rowid;
+    d.cidx = md.cidx;
+    d.val = md.val;
+    d.nnz = c->nnz;
+    d.nother = N - 1;
+    d.prec = c->prec;
+    int o = 0;
+    for (int k = 0; k < N; ++k)
+      if (k != n) d.fac[o++] = c->prec == SACD_FP32 ? (const void*)c->m[k].A : (const void*)c->m[k].A16;
+    d.R = R;
+    d.Rp = Rp;
+    d.rv = c->rv;
+    d.sub = md.sub;
+    d.tile = md.tile;
+    d.ntiles = md.ntiles;
+    d.I = md.I;
+    d.M = md.M;
+    d.carry = c->carry;
+    d.split_light = md.split_light;
+    d.nsplit_light = md.nlight;
+    d.split_heavy = md.split_heavy;
+    d.nsplit_heavy = md.nheavy;
+    d.A = md.A;
+    d.A16 = md.A16;
+    d.G = c->G;
+    d.zprev = md.zprev;
+    d.mask = nullptr;
+    d.replay = c->replay;
+    for (int k = 0; k < N; ++k) d.gram[k] = c->m[k].gram;
+    d.gram_out = md.gram;
+    d.gpart = c->gpart;
+    d.gram_blocks = (int)md.gram_blocks;
+    d.N = N;
+    d.n = n;
+    d.lnorm = c->lnorm;
+    d.fixup = c->fixup;
+    d.p1_blocks = (int)md.p1_blocks;
+    d.H = c->H;
+    d.Hf = c->Hf;
+    d.invh = c->invh;
+    d.lh = c->lh;
+    d.tipart = c->tipart;
+    d.state = c->state + (size_t)n * ST_STRIDE;
+    d.counters = c->counters;
+    d.nsel = c->nsel + n;
+  }
+  TRY(upload_descs(c));
+  // ---- fit descriptor
+  {
+    const int L = N - 1;
+    c->fit_blocks = std::max<int64_t>(1, (c->m[L].I + 255) / 256);
+    TRY(dalloc(c, &c->fitpart, c->fit_blocks));
+    TRY(dalloc(c, &c->fitout, 4));
+    TRY(dalloc(c, &c->dfit, 1));
+    FitDesc& f = c->hfit;
+    memset(&f, 0, sizeof(f));
+    f.A = c->m[L].A;
+    f.M = c->m[L].M;
+    f.I = c->m[L].I;
+    f.R = R;
+    f.Rp = Rp;
+    f.N = N;
+    for (int k = 0; k < N; ++k) f.gram[k] = c->m[k].gram;
+    f.norm_x_sq = c->norm_x_sq;
+    f.part = c->fitpart;
+    f.out = c->fitout;
+    f.counter = c->counters + 2;
+    CK(cudaMemcpyAsync(c->dfit, &f, sizeof(f), cudaMemcpyHostToDevice, c->st));
+  }
+  // ---- initial Grams
+  for (int n = 0; n < N; ++n) enqueue_gram(c, n);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  guard.ok = true;
+  *out = c;
+  return SACD_OK;
+}
+
+}  // namespace
+
+// ==========================================================================================
+// C ABI
+extern "C" {
+
+sacd_status sacd_create(const sacd_config* cfg, sacd_ctx** out) {
+  if (!out) return fail(SACD_EINVAL, "null out");
+  *out = nullptr;
+  try {
+    return create_impl(cfg, out);
+  } catch (const std::bad_alloc&) {
+    return fail(SACD_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(SACD_EINVAL, "unexpected exception");
+  }
+}
+
+sacd_status sacd_mode_step(sacd_ctx* c, int32_t mode, int64_t* n_selected) {
+  TRY(check_ctx(c));
+  if (mode < 0 || mode >= c->N) return fail(SACD_EINVAL, "mode out of range");
+  enqueue_step(c, mode);
+  if (c->replay_mode == mode) {
+    const double zero = 0.0;
+    CK(cudaMemcpyAsync(c->state + (size_t)mode * ST_STRIDE + ST_REPLAY, &zero, sizeof(double),
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->replay_mode = -1;
+  }
+  CK(cudaGetLastError());
+  c->last_mode = mode;
+  c->mlast_valid = (mode == c->N - 1);  // M of the last mode depends on every other factor
+  if (n_selected) {
+    unsigned long long v = 0;
+    CK(cudaMemcpyAsync(&v, c->nsel + mode, sizeof(v), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    *n_selected = (int64_t)v;
+  }
+  return SACD_OK;
+}
+
+sacd_status sacd_iterate(sacd_ctx* c, int32_t iters) {
+  TRY(check_ctx(c));
+  if (iters < 0) return fail(SACD_EINVAL, "iters < 0");
+  if (c->replay_mode >= 0) return fail(SACD_ESTATE, "a replay mask is pending; run sacd_mode_step first");
+  if (iters == 0) return SACD_OK;
+  if (c->prof.on) {
+    for (int it = 0; it < iters; ++it)
+      for (int n = 0; n < c->N; ++n) enqueue_step(c, n);
+    CK(cudaGetLastError());
+  } else {
+    if (!c->gexec) {
+      CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+      for (int n = 0; n < c->N; ++n) enqueue_step(c, n);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(c->st, &g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+      c->graph = g;
+      CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
+    }
+    for (int it = 0; it < iters; ++it) CK(cudaGraphLaunch(c->gexec, c->st));
+  }
+  c->last_mode = c->N - 1;
+  c->mlast_valid = true;
+  return SACD_OK;
+}
+
+sacd_status sacd_fit(sacd_ctx* c, double* objective, double* fit) {
+  TRY(check_ctx(c));
+  if (!c->mlast_valid) {
+    enqueue_mttkrp(c, c->N - 1);
+    c->mlast_valid = true;
+  }
+  {
+    KScope k(c, K_FIT);
+    launch_fit(c->dfit, c->fit_blocks, c->st);
+  }
+  double out[4];
+  CK(cudaMemcpyAsync(out, c->fitout, sizeof(out), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (objective) *objective = out[0];
+  if (fit) *fit = out[1];
+  return SACD_OK;
+}
+
+sacd_status sacd_get_factor(sacd_ctx* c, int32_t mode, float* host_out) {
+  TRY(check_ctx(c));
+  if (mode < 0 || mode >= c->N || !host_out) return fail(SACD_EINVAL, "bad mode or null output");
+  CK(cudaMemcpy2DAsync(host_out, sizeof(float) * c->R, c->m[mode].A, sizeof(float) * c->Rp, sizeof(float) * c->R,
+                       c->m[mode].I, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return SACD_OK;
+}
+
+sacd_status sacd_set_factor(sacd_ctx* c, int32_t mode, const float* host_in) {
+  TRY(check_ctx(c));
+  if (mode < 0 || mode >= c->N || !host_in) return fail(SACD_EINVAL, "bad mode or null input");
+  const int64_t I = c->m[mode].I;
+  for (int64_t e = 0; e < I * c->R; ++e)
+    if (!(host_in[e] >= 0.f) || !std::isfinite(host_in[e]))
+      return fail(SACD_EINVAL, "factor values must be finite and >= 0");
+  CK(cudaMemcpy2DAsync(c->m[mode].A, sizeof(float) * c->Rp, host_in, sizeof(float) * c->R, sizeof(float) * c->R, I,
+                       cudaMemcpyHostToDevice, c->st));
+  if (c->m[mode].A16) launch_to_bf16(c->m[mode].A, c->m[mode].A16, I * c->Rp, c->st);
+  enqueue_gram(c, mode);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  if (mode != c->N - 1) c->mlast_valid = false;
+  return SACD_OK;
+}
+
+sacd_status sacd_debug_tap(sacd_ctx* c, int32_t what, int32_t mode, void* host_out) {
+  TRY(check_ctx(c));
+  if (!host_out) return fail(SACD_EINVAL, "null output");
+  if (mode < 0 || mode >= c->N) return fail(SACD_EINVAL, "mode out of range");
+  const int R = c->R, Rp = c->Rp;
+  const ModeData& md = c->m[mode];
+  const int64_t lastI = c->last_mode >= 0 ? c->m[c->last_mode].I : 0;
+  switch (what) {
+    case SACD_TAP_M:
+      CK(cudaMemcpy2DAsync(host_out, sizeof(float) * R, md.M, sizeof(float) * Rp, sizeof(float) * R, md.I,
+                           cudaMemcpyDeviceToHost, c->st));
+      break;
+    case SACD_TAP_G:
+      if (c->last_mode < 0) return fail(SACD_ESTATE, "no mode step yet");
+      CK(cudaMemcpy2DAsync(host_out, sizeof(float) * R, c->G, sizeof(float) * Rp, sizeof(float) * R, lastI,
+                           cudaMemcpyDeviceToHost, c->st));
+      break;
+    case SACD_TAP_ZPREV:
+      CK(cudaMemcpy2DAsync(host_out, sizeof(float) * R, md.zprev, sizeof(float) * Rp, sizeof(float) * R, md.I,
+                           cudaMemcpyDeviceToHost, c->st));
+      break;
+    case SACD_TAP_MASK:
+      if (!c->debug) return fail(SACD_ESTATE, "mask recording is off (sacd_set_debug)");
+      if (c->last_mode < 0) return fail(SACD_ESTATE, "no mode step yet");
+      CK(cudaMemcpy2DAsync(host_out, R, c->mask, Rp, R, lastI, cudaMemcpyDeviceToHost, c->st));
+      break;
+    case SACD_TAP_H:
+      if (c->last_mode < 0) return fail(SACD_ESTATE, "no mode step yet");
+      CK(cudaMemcpy2DAsync(host_out, sizeof(double) * R, c->H, sizeof(double) * Rp, sizeof(double) * R, R,
+                           cudaMemcpyDeviceToHost, c->st));
+      break;
+    case SACD_TAP_GRAM:
+      CK(cudaMemcpy2DAsync(host_out, sizeof(double) * R, md.gram, sizeof(double) * Rp, sizeof(double) * R, R,
+                           cudaMemcpyDeviceToHost, c->st));
+      break;
+    case SACD_TAP_STATE: {
+      double* o = reinterpret_cast<double*>(host_out);
+      unsigned long long ns = 0;
+      CK(cudaMemcpyAsync(o, c->state + (size_t)mode * ST_STRIDE, sizeof(double) * ST_STRIDE,
+                         cudaMemcpyDeviceToHost, c->st));
+      CK(cudaMemcpyAsync(&ns, c->nsel + mode, sizeof(ns), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      o[ST_NSEL] = (double)ns;
+      o[6] = 0.0;
+      o[7] = 0.0;
+      break;
+    }
+    case SACD_TAP_CSF_ROW:
+      if (c->nnz) CK(cudaMemcpyAsync(host_out, md.rowid, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToHost, c->st));
+      break;
+    case SACD_TAP_CSF_IDX:
+      if (c->nnz)
+        CK(cudaMemcpyAsync(host_out, md.cidx, sizeof(int32_t) * c->nnz * (c->N - 1), cudaMemcpyDeviceToHost,
+                           c->st));
+      break;
+    case SACD_TAP_CSF_VAL:
+      if (c->nnz) CK(cudaMemcpyAsync(host_out, md.val, sizeof(float) * c->nnz, cudaMemcpyDeviceToHost, c->st));
+      break;
+    default:
+      return fail(SACD_EINVAL, "unknown tap");
+  }
+  CK(cudaStreamSynchronize(c->st));
+  return SACD_OK;
+}
+
+sacd_status sacd_set_debug(sacd_ctx* c, int32_t on) {
+  TRY(check_ctx(c));
+  c->debug = on != 0;
+  return upload_descs(c);
+}
+
+sacd_status sacd_replay_mask(sacd_ctx* c, int32_t mode, const uint8_t* host_mask) {
+  TRY(check_ctx(c));
+  if (mode < 0 || mode >= c->N) return fail(SACD_EINVAL, "mode out of range");
+  double flag = 0.0;
+  if (host_mask) {
+    const int64_t I = c->m[mode].I;
+    CK(cudaMemsetAsync(c->replay, 0, (size_t)I * c->Rp, c->st));
+    CK(cudaMemcpy2DAsync(c->replay, c->Rp, host_mask, c->R, c->R, I, cudaMemcpyHostToDevice, c->st));
+    flag = 1.0;
+    if (c->replay_mode >= 0 && c->replay_mode != mode) {
+      const double zero = 0.0;
+      CK(cudaMemcpyAsync(c->state + (size_t)c->replay_mode * ST_STRIDE + ST_REPLAY, &zero, sizeof(double),
+                         cudaMemcpyHostToDevice, c->st));
+    }
+    c->replay_mode = mode;
+  } else if (c->replay_mode == mode) {
+    c->replay_mode = -1;
+  }
+  CK(cudaMemcpyAsync(c->state + (size_t)mode * ST_STRIDE + ST_REPLAY, &flag, sizeof(double), cudaMemcpyHostToDevice,
+                     c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return SACD_OK;
+}
+
+sacd_status sacd_get_info(sacd_ctx* c, sacd_info* out) {
+  if (!c || !out) return fail(SACD_EINVAL, "null argument");
+  memset(out, 0, sizeof(*out));
+  out->nmodes = c->N;
+  out->rank = c->R;
+  out->rank_padded = c->Rp;
+  out->precision = c->prec;
+  for (int n = 0; n < c->N; ++n) {
+    out->dims[n] = c->dims[n];
+    out->tiles[n] = c->m[n].ntiles;
+    out->tile_nnz[n] = c->m[n].tile;
+    out->split_rows[n] = c->m[n].nlight + c->m[n].nheavy;
+  }
+  out->nnz = c->nnz;
+  out->norm_x_sq = c->norm_x_sq;
+  out->device_bytes = c->device_bytes;
+  return SACD_OK;
+}
+
+sacd_status sacd_sync(sacd_ctx* c) {
+  TRY(check_ctx(c));
+  CK(cudaStreamSynchronize(c->st));
+  return SACD_OK;
+}
+
+sacd_status sacd_profile_enable(sacd_ctx* c, int32_t on) {
+  TRY(check_ctx(c));
+  Prof& p = c->prof;
+  if (on && p.ev.empty()) {
+    p.ev.resize(4096);
+    p.cls.resize(2048);
+    for (auto& e : p.ev) CK(cudaEventCreate(&e));
+  }
+  if (on) {
+    for (int i = 0; i < K_NCLASS; ++i) {
+      p.launches[i] = 0;
+      p.ms[i] = 0.0;
+    }
+    p.used = 0;
+    p.dropped = 0;
+  }
+  p.on = on != 0;
+  return SACD_OK;
+}
+
+sacd_status sacd_profile_read(sacd_ctx* c, sacd_kernel_stat* out, int32_t cap, int32_t* n) {
+  TRY(check_ctx(c));
+  Prof& p = c->prof;
+  CK(cudaStreamSynchronize(c->st));
+  for (int i = 0; i < p.used; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]) == cudaSuccess) {
+      p.ms[p.cls[i]] += ms;
+      p.launches[p.cls[i]] += 1;
+    } else {
+      cudaGetLastError();
+      p.dropped++;
+    }
+  }
+  p.used = 0;
+  int k = 0;
+  for (int i = 0; i < K_NCLASS; ++i) {
+    if (k < cap && out) {
+      memset(out[k].name, 0, sizeof(out[k].name));
+      strncpy(out[k].name, kClassName[i], sizeof(out[k].name) - 1);
+      out[k].launches = p.launches[i];
+      out[k].total_ms = p.ms[i];
+    }
+    ++k;
+  }
+  if (n) *n = k;
+  return SACD_OK;
+}
+
+void sacd_destroy(sacd_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  invalidate_graph(c);
+  for (auto& e : c->prof.ev) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+  cudaGetLastError();
+  delete c;
+}
+
+const char* sacd_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

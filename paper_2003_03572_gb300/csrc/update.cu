@@ -1,0 +1,595 @@
+// The part of a SaCD mode step that follows the MTTKRP (Algorithm 1, one factor block):
+//   hl     H = Hadamard of the other Grams (Eq. 10), L = ||H|| (Algorithm 1), 1/h_rr, L/2
+//   pass1  G = A H - M (Eq. 9, 14), z (Eq. 20) for every element, ti = sum z (Eq. 25); the last
+//          block picks the selection branch (first visit / Eq. 24 / Eq. 27)
+//   pass2  selection and the projected update of the selected elements (Eq. 11-13), columns in
+//          order within a row, with the gradient fix-up; z^{k-1} <- z; BF16 mirror refresh
+//   gram   A^T A of the updated factor, FP64 result from compensated FP32 products and sums;
+//          gram_reduce sums the per-block partials
+//   fit    f = ||X||^2 - 2 <X, model> + ||model||^2 (Eq. 6-8) in FP64
+// GB300 runs FP64 at a small fraction of its FP32 rate, so the sums that decide accuracy
+// (A H - M under cancellation, the Gauss-Seidel gradient, the Grams) use error-free FP32
+// transformations (exact products and sums carried as (hi, lo) pairs) instead of FP64 FMAs.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sacd {
+
+// ------------------------------------------------------------------------------------------
+// block reductions with a fixed shape (deterministic)
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x >> 1; w >= 1; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  T r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------------------------------------
+// H, L, 1/h, L/2
+__global__ void __launch_bounds__(256) hl_kernel(const StepDesc* __restrict__ descs) {
+  const StepDesc* __restrict__ dp = descs + blockIdx.x;
+  __shared__ double red[256];
+  __shared__ double v[SACD_MAXR];
+  __shared__ const double* grams[SACD_MAXN];
+  const int R = dp->R, Rp = dp->Rp, N = dp->N, n = dp->n, lnorm = dp->lnorm;
+  double* __restrict__ H = dp->H;
+  float* __restrict__ Hf = dp->Hf;
+  if (threadIdx.x < SACD_MAXN) grams[threadIdx.x] = threadIdx.x < N ? dp->gram[threadIdx.x] : nullptr;
+  __syncthreads();
+  double ss = 0.0;
+  for (int e = threadIdx.x; e < Rp * Rp; e += blockDim.x) {
+    const int i = e / Rp, j = e - (e / Rp) * Rp;
+    double h = 0.0;
+    if (i < R && j < R) {
+      h = 1.0;
+      for (int k = 0; k < N; ++k)
+        if (k != n) h *= __ldg(grams[k] + e);
+    }
+    H[e] = h;
+    Hf[e] = (float)h;
+    ss += h * h;
+  }
+  const double Lfro = sqrt(block_sum(ss, red));
+  double L = Lfro;
+  if (lnorm == 1 && R > 0) {
+    // largest eigenvalue of the symmetric PSD matrix H by power iteration
+    for (int i = threadIdx.x; i < R; i += blockDim.x) v[i] = 1.0 / sqrt((double)R);
+    __syncthreads();
+    double lam = 0.0;
+    for (int it = 0; it < 500; ++it) {
+      double w = 0.0;
+      const int i = threadIdx.x;
+      if (i < R) {
+        for (int j = 0; j < R; ++j) w += H[i * Rp + j] * v[j];
+      }
+      const double nn = sqrt(block_sum(i < R ? w * w : 0.0, red));
+      if (i < R) v[i] = nn > 0 ? w / nn : 0.0;
+      __syncthreads();
+      const bool done = fabs(nn - lam) <= 1e-15 * nn;
+      lam = nn;
+      if (done) break;
+    }
+    L = lam;
+  }
+  for (int r = threadIdx.x; r < Rp; r += blockDim.x) {
+    float ih = 0.f, lhv = 0.f;
+    if (r < R) {
+      double h = 1.0;
+      for (int k = 0; k < N; ++k)
+        if (k != n) h *= __ldg(grams[k] + r * Rp + r);
+      if (h > 0.0) ih = (float)(1.0 / h);
+      lhv = (float)(0.5 * (lnorm == 2 ? h : L));
+    }
+    dp->invh[r] = ih;
+    dp->lh[r] = lhv;
+  }
+  if (threadIdx.x == 0) {
+    dp->state[ST_L] = (lnorm == 2) ? 0.0 : L;
+    *dp->nsel = 0ull;
+  }
+}
+
+void launch_hl(const StepDesc* d_descs, int njobs, cudaStream_t st) {
+  hl_kernel<<<njobs, 256, 0, st>>>(d_descs);
+}
+
+// Row passes: 256 threads per block, TPR = Rp/8 threads per row, each thread owns 8 adjacent
+// columns of one row; RB = 256/TPR rows per block.
+int rows_per_block(int Rp) { return 256 / (Rp / 8); }
+int rows_per_block_pass1(int Rp) { return rows_per_block(Rp); }
+int rows_per_block_pass2(int Rp) { return rows_per_block(Rp); }
+static size_t pass_smem_bytes(int Rp) {
+  const int RB = rows_per_block(Rp);
+  size_t b = (size_t)RB * (Rp + 1) * sizeof(float);  // staged A rows
+  if (Rp <= 64) b += (size_t)Rp * Rp * sizeof(float);  // H
+  b += (size_t)RB * 32;                                // selection bytes (pass 2)
+  return (b + 15) / 16 * 16;
+}
+
+// stage `nrows` rows of an I x Rp matrix into shared memory with row stride Rp+1
+__device__ __forceinline__ void stage_rows(const float* __restrict__ src, float* dst, int nrows, int Rp) {
+  const int ST = Rp + 1;
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  const int n4 = nrows * Rp / 4;
+  for (int e = threadIdx.x; e < n4; e += blockDim.x) {
+    const float4 v = s4[e];
+    const int f = e * 4;
+    const int r = f / Rp, c = f - r * Rp;
+    float* p = dst + r * ST + c;
+    p[0] = v.x; p[1] = v.y; p[2] = v.z; p[3] = v.w;
+  }
+}
+
+// compensated (hi, lo) accumulation of a*b
+__device__ __forceinline__ void dot2_acc(float a, float b, float& hi, float& lo) {
+  float p, e, s, t;
+  two_prod(a, b, p, e);
+  two_sum(hi, p, s, t);
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(t, e));
+}
+
+// ------------------------------------------------------------------------------------------
+// pass 1: G = A H - M with compensated dot products (rounded once to FP32), z, ti
+__global__ void __launch_bounds__(256) pass1_kernel(const StepDesc* __restrict__ descs,
+                                                   const int64_t* __restrict__ base, int njobs) {
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  __shared__ double red[256];
+  __shared__ int amlast;
+  const int64_t gb = blockIdx.x;
+  const int jb = njobs > 1 ? find_job(base, njobs, gb) : 0;
+  const StepDesc* __restrict__ dp = descs + jb;
+  const int64_t lb = gb - base[jb];
+  const int R = dp->R, Rp = dp->Rp, ST = Rp + 1;
+  const int64_t I = dp->I;
+  const float* __restrict__ A = dp->A;
+  const float* __restrict__ M = dp->M;
+  float* __restrict__ G = dp->G;
+  const float* __restrict__ invh = dp->invh;
+  const float* __restrict__ lh = dp->lh;
+  const int TPR = Rp >> 3, RB = 256 / TPR;
+  const int64_t row0 = lb * RB;
+  const int nrows = (int)min((int64_t)RB, I - row0);
+  float* As = sm;
+  float* Hs = sm + RB * ST;
+  const float* __restrict__ Hsrc = dp->Hf;
+  stage_rows(A + row0 * Rp, As, nrows, Rp);
+  if (Rp <= 64) {
+    for (int e = threadIdx.x; e < Rp * Rp / 4; e += blockDim.x)
+      reinterpret_cast<float4*>(Hs)[e] = __ldg(reinterpret_cast<const float4*>(Hsrc) + e);
+  }
+  const float* Hr = Rp <= 64 ? Hs : Hsrc;
+  __syncthreads();
+  const int rl = threadIdx.x / TPR, c0 = (threadIdx.x % TPR) * 8;
+  float zsum = 0.f;
+  if (rl < nrows && c0 < R) {
+    const int64_t row = row0 + rl;
+    const float4* m4 = reinterpret_cast<const float4*>(M + row * Rp + c0);
+    const float4 m0 = m4[0], m1 = m4[1];
+    float hi[8] = {-m0.x, -m0.y, -m0.z, -m0.w, -m1.x, -m1.y, -m1.z, -m1.w};
+    float lo[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float* arow = As + rl * ST;
+    for (int j = 0; j < R; ++j) {
+      const float aj = arow[j];
+      const float4 h0 = *reinterpret_cast<const float4*>(Hr + j * Rp + c0);
+      const float4 h1 = *reinterpret_cast<const float4*>(Hr + j * Rp + c0 + 4);
+      dot2_acc(aj, h0.x, hi[0], lo[0]); dot2_acc(aj, h0.y, hi[1], lo[1]);
+      dot2_acc(aj, h0.z, hi[2], lo[2]); dot2_acc(aj, h0.w, hi[3], lo[3]);
+      dot2_acc(aj, h1.x, hi[4], lo[4]); dot2_acc(aj, h1.y, hi[5], lo[5]);
+      dot2_acc(aj, h1.z, hi[6], lo[6]); dot2_acc(aj, h1.w, hi[7], lo[7]);
+    }
+    float g[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      g[u] = __fadd_rn(hi[u], lo[u]);
+      const int c = c0 + u;
+      if (c < R) {
+        const float s = sacd_step(arow[c], g[u], __ldg(invh + c));
+        zsum += sacd_importance(g[u], s, __ldg(lh + c));
+      } else {
+        g[u] = 0.f;
+      }
+    }
+    float4* g4 = reinterpret_cast<float4*>(G + row * Rp + c0);
+    g4[0] = make_float4(g[0], g[1], g[2], g[3]);
+    g4[1] = make_float4(g[4], g[5], g[6], g[7]);
+  }
+  const double bz = block_sum((double)zsum, red);
+  if (threadIdx.x == 0) {
+    dp->tipart[lb] = bz;
+    __threadfence();
+    const unsigned prev = atomicAdd(&dp->counters[0], 1u);
+    amlast = (prev == (unsigned)dp->p1_blocks - 1u);
+  }
+  __syncthreads();
+  if (amlast) {
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < dp->p1_blocks; i += blockDim.x) s += __ldcg(dp->tipart + i);
+    const double ti = block_sum(s, red);
+    if (threadIdx.x == 0) {
+      double* stt = dp->state;
+      const bool first = stt[ST_FIRST] != 0.0;
+      const double branch = first ? 0.0 : (ti > stt[ST_TIPREV] ? 2.0 : 1.0);
+      stt[ST_TI] = ti;
+      stt[ST_BRANCH] = branch;
+      stt[ST_TIPREV] = ti;
+      stt[ST_FIRST] = 0.0;
+      dp->counters[0] = 0u;
+    }
+  }
+}
+
+void launch_pass1(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+                  cudaStream_t st) {
+  if (total_blocks <= 0) return;
+  pass1_kernel<<<(unsigned)total_blocks, 256, pass_smem_bytes(Rp), st>>>(d_descs, d_base, njobs);
+}
+
+// ------------------------------------------------------------------------------------------
+// pass 2: phase A (element-parallel): z from the stored gradient, selection, z^{k-1} <- z.
+// phase B (one warp per row that has a selected element): the selected columns in order,
+// s = max(0, u - g/h) - u (Eq. 12-13). With the Gauss-Seidel fix-up the gradient of a column is
+// recomputed from the current row, g = a_cur . H[:, r] - m_r, as a compensated warp dot product
+// (exact products, error-free sums across lanes), so later columns see the exact gradient
+// without an accumulated chain of FP32 roundings.
+__global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__ descs,
+                                                   const int64_t* __restrict__ base, int njobs) {
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  __shared__ long long cred[256];
+  const int64_t gb = blockIdx.x;
+  const int jb = njobs > 1 ? find_job(base, njobs, gb) : 0;
+  const StepDesc* __restrict__ dp = descs + jb;
+  const int64_t lb = gb - base[jb];
+  const int R = dp->R, Rp = dp->Rp, ST = Rp + 1;
+  const int64_t I = dp->I;
+  float* __restrict__ A = dp->A;
+  const float* __restrict__ M = dp->M;
+  const float* __restrict__ G = dp->G;
+  float* __restrict__ zprev = dp->zprev;
+  const float* __restrict__ invh = dp->invh;
+  const float* __restrict__ lh = dp->lh;
+  uint8_t* __restrict__ mask = dp->mask;
+  const int TPR = Rp >> 3, RB = 256 / TPR;
+  const int64_t row0 = lb * RB;
+  const int nrows = (int)min((int64_t)RB, I - row0);
+  float* As = sm;
+  float* Hs = sm + RB * ST;
+  uint8_t* selb = reinterpret_cast<uint8_t*>(sm + RB * ST + (Rp <= 64 ? Rp * Rp : 0));
+  const float* __restrict__ Hsrc = dp->Hf;
+  stage_rows(A + row0 * Rp, As, nrows, Rp);
+  if (Rp <= 64) {
+    for (int e = threadIdx.x; e < Rp * Rp / 4; e += blockDim.x)
+      reinterpret_cast<float4*>(Hs)[e] = __ldg(reinterpret_cast<const float4*>(Hsrc) + e);
+  }
+  const float* Hr = Rp <= 64 ? Hs : Hsrc;
+  __syncthreads();
+  const int branch = (int)dp->state[ST_BRANCH];
+  const bool replay = dp->state[ST_REPLAY] != 0.0;
+  const int rl = threadIdx.x / TPR, ch = threadIdx.x % TPR, c0 = ch * 8;
+  long long count = 0;
+  // ---- phase A
+  if (rl < nrows) {
+    const int64_t row = row0 + rl;
+    unsigned bits = 0;
+    if (c0 < R) {
+      const float4* g4 = reinterpret_cast<const float4*>(G + row * Rp + c0);
+      float4* z4 = reinterpret_cast<float4*>(zprev + row * Rp + c0);
+      const float4 ga = g4[0], gb4 = g4[1], za = z4[0], zb = z4[1];
+      const float gv[8] = {ga.x, ga.y, ga.z, ga.w, gb4.x, gb4.y, gb4.z, gb4.w};
+      const float zp[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+      float zn[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = c0 + u;
+        zn[u] = zp[u];
+        if (c < R) {
+          const float a = As[rl * ST + c];
+          const float s0 = sacd_step(a, gv[u], __ldg(invh + c));
+          const float z = sacd_importance(gv[u], s0, __ldg(lh + c));
+          bool sel;
+          if (replay) sel = dp->replay[row * Rp + c] != 0;
+          else if (branch == 0) sel = z > 0.f;                    // first visit: z > 0
+          else if (branch == 2) sel = __fsub_rn(zp[u], z) > 0.f;  // Eq. 27: sp = z^{k-1} - z^k
+          else sel = __fsub_rn(z, zp[u]) > 0.f;                   // Eq. 24: sp = z^k - z^{k-1}
+          zn[u] = z;
+          if (sel) bits |= 1u << u;
+        }
+      }
+      z4[0] = make_float4(zn[0], zn[1], zn[2], zn[3]);
+      z4[1] = make_float4(zn[4], zn[5], zn[6], zn[7]);
+      if (mask) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (c0 + u < R) mask[row * Rp + c0 + u] = (bits >> u) & 1u;
+      }
+    }
+    selb[rl * TPR + ch] = (uint8_t)bits;
+    count = __popc(bits);
+  }
+  const long long tot = block_sum(count, cred);  // also orders phase A before phase B
+  if (threadIdx.x == 0 && tot) atomicAdd(dp->nsel, (unsigned long long)tot);
+  if (tot == 0) return;
+  // ---- phase B
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  const bool gs = dp->fixup == 0;
+  const int CPL = Rp > 32 ? Rp / 32 : 1;
+  __nv_bfloat16* __restrict__ A16 = dp->A16;
+  for (int r2 = warp; r2 < nrows; r2 += 8) {
+    bool any = false;
+    for (int k = 0; k < TPR; ++k) any |= selb[r2 * TPR + k] != 0;
+    if (!any) continue;
+    const int64_t row = row0 + r2;
+    float* arow = As + r2 * ST;
+    bool upd = false;
+    for (int r = 0; r < R; ++r) {
+      if (!((selb[r2 * TPR + (r >> 3)] >> (r & 7)) & 1u)) continue;
+      const float ar = arow[r];
+      float g;
+      if (gs && upd) {
+        float hi = 0.f, lo = 0.f;
+        for (int k = 0; k < CPL; ++k) {
+          const int j = lane + 32 * k;
+          if (j < R) dot2_acc(arow[j], Hr[r * Rp + j], hi, lo);  // H is symmetric: H[j][r] = H[r][j]
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+          const float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
+          const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
+          float s, t;
+          two_sum(hi, ohi, s, t);
+          hi = s;
+          lo = __fadd_rn(__fadd_rn(lo, olo), t);
+        }
+        float s, t;
+        two_sum(hi, -__ldg(M + row * Rp + r), s, t);
+        g = __fadd_rn(s, __fadd_rn(lo, t));
+      } else {
+        g = __ldg(G + row * Rp + r);
+      }
+      const float s = sacd_step(ar, g, __ldg(invh + r));
+      if (s != 0.f) {
+        __syncwarp();
+        if (lane == 0) arow[r] = __fadd_rn(ar, s);
+        __syncwarp();
+        upd = true;
+      }
+    }
+    if (upd) {
+      for (int c = lane; c < Rp; c += 32) {
+        const float v = arow[c];
+        A[row * Rp + c] = v;
+        if (A16) A16[row * Rp + c] = __float2bfloat16_rn(v);
+      }
+    }
+  }
+}
+
+void launch_pass2(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+                  cudaStream_t st) {
+  if (total_blocks <= 0) return;
+  pass2_kernel<<<(unsigned)total_blocks, 256, pass_smem_bytes(Rp), st>>>(d_descs, d_base, njobs);
+}
+
+// ------------------------------------------------------------------------------------------
+// Gram A^T A. Each product is split exactly (two_prod) and summed with two_sum into an FP32
+// (hi, lo) pair per output entry ("Dot2", Ogita-Rump-Oishi 2005); every staged chunk of rows is
+// flushed into an FP64 accumulator; each block writes its FP64 partial, and gram_reduce sums
+// the partials in block order with a fixed-shape tree.
+__host__ __device__ int gram_chunk_rows(int Rp) { return 4096 / Rp; }
+
+template <int TS>
+__device__ void gram_tile_pass(const StepDesc* __restrict__ dp, int64_t lb, int oi, int oj, int TD, float* As,
+                               double* out) {
+  const int Rp = dp->Rp;
+  const int64_t I = dp->I;
+  const int nb = dp->gram_blocks;
+  const float* __restrict__ A = dp->A;
+  const int CH = gram_chunk_rows(Rp);
+  const int ti = threadIdx.x / TD, tj = threadIdx.x - (threadIdx.x / TD) * TD;
+  const bool active = threadIdx.x < TD * TD;
+  const int i0 = oi * TD * TS + ti * TS, j0 = oj * TD * TS + tj * TS;
+  double accd[TS][TS];
+#pragma unroll
+  for (int x = 0; x < TS; ++x)
+#pragma unroll
+    for (int y = 0; y < TS; ++y) accd[x][y] = 0.0;
+  for (int64_t chunk = lb; chunk * CH < I; chunk += nb) {
+    const int64_t r0 = chunk * CH;
+    const int nr = (int)min((int64_t)CH, I - r0);
+    const float4* src = reinterpret_cast<const float4*>(A + r0 * Rp);
+    float4* dst = reinterpret_cast<float4*>(As);
+    for (int e = threadIdx.x; e < nr * Rp / 4; e += blockDim.x) dst[e] = src[e];
+    __syncthreads();
+    if (active) {
+      float hi[TS][TS], lo[TS][TS];
+#pragma unroll
+      for (int x = 0; x < TS; ++x)
+#pragma unroll
+        for (int y = 0; y < TS; ++y) hi[x][y] = lo[x][y] = 0.f;
+      for (int r = 0; r < nr; ++r) {
+        float ai[TS], aj[TS];
+#pragma unroll
+        for (int x = 0; x < TS; ++x) ai[x] = As[r * Rp + i0 + x];
+#pragma unroll
+        for (int y = 0; y < TS; ++y) aj[y] = As[r * Rp + j0 + y];
+#pragma unroll
+        for (int x = 0; x < TS; ++x)
+#pragma unroll
+          for (int y = 0; y < TS; ++y) dot2_acc(ai[x], aj[y], hi[x][y], lo[x][y]);
+      }
+#pragma unroll
+      for (int x = 0; x < TS; ++x)
+#pragma unroll
+        for (int y = 0; y < TS; ++y) accd[x][y] += (double)hi[x][y] + (double)lo[x][y];
+    }
+    __syncthreads();
+  }
+  if (active) {
+#pragma unroll
+    for (int x = 0; x < TS; ++x)
+#pragma unroll
+      for (int y = 0; y < TS; ++y) out[(int64_t)(i0 + x) * Rp + (j0 + y)] = accd[x][y];
+  }
+}
+
+template <int TS>
+__global__ void __launch_bounds__(256) gram_kernel(const StepDesc* __restrict__ descs,
+                                                  const int64_t* __restrict__ base, int njobs) {
+  __shared__ float4 As4[1024];  // 16 KB: gram_chunk_rows(Rp) rows of Rp floats
+  float* As = reinterpret_cast<float*>(As4);
+  const int64_t gb = blockIdx.x;
+  const int jb = njobs > 1 ? find_job(base, njobs, gb) : 0;
+  const StepDesc* __restrict__ dp = descs + jb;
+  const int64_t lb = gb - base[jb];
+  const int Rp = dp->Rp;
+  const int TD = Rp >= 16 ? 16 : Rp;
+  const int OB = Rp / (TD * TS);
+  double* out = dp->gpart + lb * (int64_t)Rp * Rp;
+  for (int oi = 0; oi < OB; ++oi)
+    for (int oj = 0; oj < OB; ++oj) gram_tile_pass<TS>(dp, lb, oi, oj, TD, As, out);
+}
+
+// sum of the per-block partials: 32 entries per block, 8 partial lanes each, fixed tree
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const StepDesc* __restrict__ descs,
+                                                         const int64_t* __restrict__ base, int njobs) {
+  __shared__ double red[8][32];
+  const int64_t gb = blockIdx.x;
+  const int jb = njobs > 1 ? find_job(base, njobs, gb) : 0;
+  const StepDesc* __restrict__ dp = descs + jb;
+  const int Rp = dp->Rp;
+  const int nb = dp->gram_blocks;
+  const int64_t e = (gb - base[jb]) * 32 + (threadIdx.x & 31);
+  const int p = threadIdx.x >> 5;
+  double s = 0.0;
+  if (e < (int64_t)Rp * Rp)
+    for (int b = p; b < nb; b += 8) s += dp->gpart[(int64_t)b * Rp * Rp + e];
+  red[p][threadIdx.x & 31] = s;
+  __syncthreads();
+  for (int w = 4; w >= 1; w >>= 1) {
+    if (p < w) red[p][threadIdx.x & 31] += red[p + w][threadIdx.x & 31];
+    __syncthreads();
+  }
+  if (p == 0 && e < (int64_t)Rp * Rp) dp->gram_out[e] = red[0][threadIdx.x & 31];
+}
+
+void launch_gram(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+                 cudaStream_t st) {
+  if (total_blocks <= 0) return;
+  if (Rp <= 16)
+    gram_kernel<1><<<(unsigned)total_blocks, 256, 0, st>>>(d_descs, d_base, njobs);
+  else if (Rp == 32)
+    gram_kernel<2><<<(unsigned)total_blocks, 256, 0, st>>>(d_descs, d_base, njobs);
+  else
+    gram_kernel<4><<<(unsigned)total_blocks, 256, 0, st>>>(d_descs, d_base, njobs);
+}
+
+int gram_reduce_blocks(int Rp) { return (Rp * Rp + 31) / 32; }
+
+void launch_gram_reduce(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks,
+                        cudaStream_t st) {
+  if (total_blocks <= 0) return;
+  gram_reduce_kernel<<<(unsigned)total_blocks, 256, 0, st>>>(d_descs, d_base, njobs);
+}
+
+// ------------------------------------------------------------------------------------------
+// objective and fit
+__global__ void __launch_bounds__(256) fit_kernel(const FitDesc* __restrict__ fdp) {
+  const FitDesc& f = *fdp;
+  __shared__ double red[256];
+  __shared__ int amlast;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double part = 0.0;
+  if (i < f.I) {
+    float hi = 0.f, lo = 0.f;
+    const float* a = f.A + i * f.Rp;
+    const float* m = f.M + i * f.Rp;
+    for (int r = 0; r < f.R; ++r) {
+      float p, e, s, t;
+      two_prod(a[r], m[r], p, e);
+      two_sum(hi, p, s, t);
+      hi = s;
+      lo = __fadd_rn(lo, __fadd_rn(t, e));
+    }
+    part = (double)hi + (double)lo;
+  }
+  const double bs = block_sum(part, red);
+  if (threadIdx.x == 0) {
+    f.part[blockIdx.x] = bs;
+    __threadfence();
+    const unsigned prev = atomicAdd(f.counter, 1u);
+    amlast = (prev == gridDim.x - 1u);
+  }
+  __syncthreads();
+  if (amlast) {
+    __threadfence();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(f.part + b);
+    const double inner = block_sum(s, red);
+    double mn = 0.0;
+    for (int e = threadIdx.x; e < f.R * f.R; e += blockDim.x) {
+      const int r = e / f.R, c = e - (e / f.R) * f.R;
+      double p = 1.0;
+      for (int k = 0; k < f.N; ++k) p *= f.gram[k][r * f.Rp + c];
+      mn += p;
+    }
+    const double mnorm = block_sum(mn, red);
+    if (threadIdx.x == 0) {
+      const double obj = f.norm_x_sq - 2.0 * inner + mnorm;
+      f.out[0] = obj;
+      f.out[1] = f.norm_x_sq > 0 ? 1.0 - sqrt(fmax(obj, 0.0)) / sqrt(f.norm_x_sq) : 0.0;
+      f.out[2] = inner;
+      f.out[3] = mnorm;
+      *f.counter = 0u;
+    }
+  }
+}
+
+void launch_fit(const FitDesc* d_fit, int64_t blocks, cudaStream_t st) {
+  fit_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(d_fit);
+}
+
+// ------------------------------------------------------------------------------------------
+__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __float2bfloat16_rn(src[i]);
+}
+void launch_to_bf16(const float* src, void* dst, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  const int64_t blocks = min((n + 255) / 256, (int64_t)152 * 16);
+  to_bf16_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, reinterpret_cast<__nv_bfloat16*>(dst), n);
+}
+
+__global__ void check_factor_kernel(const float* __restrict__ A, int64_t rows, int R, int Rp,
+                                    unsigned int* bad) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * R;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / R;
+    const int r = (int)(e - i * R);
+    const float v = A[i * Rp + r];
+    if (!(v >= 0.f) || !isfinite(v)) atomicOr(bad, 1u);
+  }
+}
+void launch_check_factor(const float* A, int64_t rows, int R, int Rp, unsigned int* bad, cudaStream_t st) {
+  if (rows * R <= 0) return;
+  const int64_t blocks = min((rows * R + 255) / 256, (int64_t)152 * 8);
+  check_factor_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, rows, R, Rp, bad);
+}
+
+void configure_kernels() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(pass1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  cudaFuncSetAttribute(pass2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  done = true;
+}
+
+}  // namespace sacd

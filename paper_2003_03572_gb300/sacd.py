@@ -1,0 +1,359 @@
+"""Thin ctypes binding of libsacd.so (C ABI in include/sacd.h), with the same entry-point names.
+
+Argument marshalling only: every step of SaCD runs in the library's CUDA kernels. There is no
+CPU fallback; if the library is missing or a GPU is absent the calls raise.
+
+Inputs may be numpy arrays (host) or CUDA tensors from PyTorch (device pointers are passed with
+``inputs_on_device=1``; PyTorch is only used here as a source of device memory and streams).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+__all__ = [
+    "SacdError",
+    "SACD_FP32",
+    "SACD_BF16_GATHER",
+    "SACD_LNORM_FRO",
+    "SACD_LNORM_SPECTRAL",
+    "SACD_LNORM_GCD",
+    "SACD_FIXUP_COLUMN_GS",
+    "SACD_FIXUP_LEMMA2",
+    "TAPS",
+    "lib",
+    "lib_path",
+    "sacd_create",
+    "sacd_mode_step",
+    "sacd_iterate",
+    "sacd_fit",
+    "sacd_get_factor",
+    "sacd_set_factor",
+    "sacd_debug_tap",
+    "sacd_set_debug",
+    "sacd_replay_mask",
+    "sacd_get_info",
+    "sacd_sync",
+    "sacd_profile_enable",
+    "sacd_profile_read",
+    "sacd_destroy",
+    "sacd_last_error",
+    "SaCD",
+]
+
+SACD_FP32, SACD_BF16_GATHER = 0, 1
+SACD_LNORM_FRO, SACD_LNORM_SPECTRAL, SACD_LNORM_GCD = 0, 1, 2
+SACD_FIXUP_COLUMN_GS, SACD_FIXUP_LEMMA2 = 0, 1
+TAPS = {"M": 0, "G": 1, "ZPREV": 2, "MASK": 3, "H": 4, "GRAM": 5, "STATE": 6, "CSF_ROW": 7, "CSF_IDX": 8, "CSF_VAL": 9}
+_STATUS = {0: "SACD_OK", 1: "SACD_EINVAL", 2: "SACD_ENOMEM", 3: "SACD_ECUDA", 4: "SACD_ETIMEOUT", 5: "SACD_ESTATE"}
+
+
+class SacdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sacd_config(C.Structure):
+    _fields_ = [
+        ("nmodes", C.c_int32),
+        ("dims", C.POINTER(C.c_int64)),
+        ("nnz", C.c_int64),
+        ("idx", C.POINTER(C.c_void_p)),
+        ("vals", C.c_void_p),
+        ("rank", C.c_int32),
+        ("init", C.POINTER(C.c_void_p)),
+        ("seed", C.c_uint64),
+        ("precision", C.c_int32),
+        ("lnorm", C.c_int32),
+        ("fixup", C.c_int32),
+        ("inputs_on_device", C.c_int32),
+        ("stream", C.c_void_p),
+    ]
+
+
+class sacd_info(C.Structure):
+    _fields_ = [
+        ("nmodes", C.c_int32),
+        ("rank", C.c_int32),
+        ("rank_padded", C.c_int32),
+        ("precision", C.c_int32),
+        ("dims", C.c_int64 * 8),
+        ("nnz", C.c_int64),
+        ("norm_x_sq", C.c_double),
+        ("device_bytes", C.c_int64),
+        ("tiles", C.c_int64 * 8),
+        ("tile_nnz", C.c_int64 * 8),
+        ("split_rows", C.c_int64 * 8),
+    ]
+
+
+class sacd_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
+_LIB = None
+
+
+def lib_path():
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsacd.so")
+
+
+def lib():
+    """Load libsacd.so (built in-tree by __graft_entry__.build()). Raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sigs = {
+        "sacd_create": (C.c_int, [C.POINTER(sacd_config), C.POINTER(vp)]),
+        "sacd_mode_step": (C.c_int, [vp, i32, C.POINTER(i64)]),
+        "sacd_iterate": (C.c_int, [vp, i32]),
+        "sacd_fit": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(dbl)]),
+        "sacd_get_factor": (C.c_int, [vp, i32, vp]),
+        "sacd_set_factor": (C.c_int, [vp, i32, vp]),
+        "sacd_debug_tap": (C.c_int, [vp, i32, i32, vp]),
+        "sacd_set_debug": (C.c_int, [vp, i32]),
+        "sacd_replay_mask": (C.c_int, [vp, i32, vp]),
+        "sacd_get_info": (C.c_int, [vp, C.POINTER(sacd_info)]),
+        "sacd_sync": (C.c_int, [vp]),
+        "sacd_profile_enable": (C.c_int, [vp, i32]),
+        "sacd_profile_read": (C.c_int, [vp, C.POINTER(sacd_kernel_stat), i32, C.POINTER(i32)]),
+        "sacd_destroy": (None, [vp]),
+        "sacd_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def sacd_last_error():
+    return lib().sacd_last_error().decode()
+
+
+def _check(status):
+    if status != 0:
+        raise SacdError(status, sacd_last_error())
+
+
+def _ptr(a):
+    """Device pointer of a CUDA tensor, or host pointer of a contiguous numpy array."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def sacd_create(dims, idx, vals, rank, init=None, *, seed=0, precision=SACD_FP32, lnorm=SACD_LNORM_FRO,
+                fixup=SACD_FIXUP_COLUMN_GS, stream=None, on_device=False):
+    """Create a context. ``idx``: sequence of N int32 arrays (or an (N, nnz) array), ``vals``:
+    float32 (nnz,), ``init``: N float32 (I_n, R) arrays or None. With ``on_device`` the arrays are
+    CUDA tensors. Returns the opaque context handle (an int)."""
+    N = len(dims)
+    keep = []
+    if on_device:
+        idx_list = [idx[n] for n in range(N)]
+        vals_a = vals
+        init_list = None if init is None else [init[n] for n in range(N)]
+        nnz = int(vals_a.numel())
+    else:
+        idx_list = [np.ascontiguousarray(idx[n], dtype=np.int32) for n in range(N)]
+        vals_a = np.ascontiguousarray(vals, dtype=np.float32)
+        init_list = None if init is None else [np.ascontiguousarray(a, dtype=np.float32) for a in init]
+        nnz = int(vals_a.shape[0])
+    keep += idx_list + [vals_a] + (init_list or [])
+    dims_a = (C.c_int64 * N)(*[int(d) for d in dims])
+    idx_p = (C.c_void_p * N)(*[_ptr(a) for a in idx_list])
+    init_p = None if init_list is None else (C.c_void_p * N)(*[_ptr(a) for a in init_list])
+    cfg = sacd_config()
+    cfg.nmodes = N
+    cfg.dims = dims_a
+    cfg.nnz = nnz
+    cfg.idx = idx_p
+    cfg.vals = _ptr(vals_a) if nnz else None
+    cfg.rank = int(rank)
+    cfg.init = init_p
+    cfg.seed = int(seed) & (2**64 - 1)
+    cfg.precision = int(precision)
+    cfg.lnorm = int(lnorm)
+    cfg.fixup = int(fixup)
+    cfg.inputs_on_device = 1 if on_device else 0
+    cfg.stream = stream
+    out = C.c_void_p()
+    _check(lib().sacd_create(C.byref(cfg), C.byref(out)))
+    del keep
+    return out.value
+
+
+def sacd_mode_step(ctx, mode, want_count=True):
+    n = C.c_int64(0)
+    _check(lib().sacd_mode_step(ctx, int(mode), C.byref(n) if want_count else None))
+    return int(n.value) if want_count else None
+
+
+def sacd_iterate(ctx, iters):
+    _check(lib().sacd_iterate(ctx, int(iters)))
+
+
+def sacd_fit(ctx):
+    o, f = C.c_double(), C.c_double()
+    _check(lib().sacd_fit(ctx, C.byref(o), C.byref(f)))
+    return o.value, f.value
+
+
+def sacd_get_info(ctx):
+    info = sacd_info()
+    _check(lib().sacd_get_info(ctx, C.byref(info)))
+    N = info.nmodes
+    return dict(
+        nmodes=N,
+        rank=info.rank,
+        rank_padded=info.rank_padded,
+        precision=info.precision,
+        dims=list(info.dims)[:N],
+        nnz=info.nnz,
+        norm_x_sq=info.norm_x_sq,
+        device_bytes=info.device_bytes,
+        tiles=list(info.tiles)[:N],
+        tile_nnz=list(info.tile_nnz)[:N],
+        split_rows=list(info.split_rows)[:N],
+    )
+
+
+def sacd_get_factor(ctx, mode, out=None):
+    info = sacd_get_info(ctx)
+    shape = (info["dims"][mode], info["rank"])
+    if out is None:
+        out = np.empty(shape, dtype=np.float32)
+    _check(lib().sacd_get_factor(ctx, int(mode), out.ctypes.data))
+    return out
+
+
+def sacd_set_factor(ctx, mode, A):
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    _check(lib().sacd_set_factor(ctx, int(mode), A.ctypes.data))
+
+
+def sacd_debug_tap(ctx, what, mode=0, last_mode=None):
+    """Copy one piece of device state to a new numpy array (see sacd_tap in include/sacd.h)."""
+    info = sacd_get_info(ctx)
+    w = TAPS[what] if isinstance(what, str) else int(what)
+    R = info["rank"]
+    N = info["nmodes"]
+    lm = mode if last_mode is None else last_mode
+    if w in (0, 2):
+        out = np.empty((info["dims"][mode], R), np.float32)
+    elif w == 1:
+        out = np.empty((info["dims"][lm], R), np.float32)
+    elif w == 3:
+        out = np.empty((info["dims"][lm], R), np.uint8)
+    elif w in (4, 5):
+        out = np.empty((R, R), np.float64)
+    elif w == 6:
+        out = np.empty(8, np.float64)
+    elif w == 7:
+        out = np.empty(info["nnz"], np.int32)
+    elif w == 8:
+        out = np.empty((N - 1, info["nnz"]), np.int32)
+    elif w == 9:
+        out = np.empty(info["nnz"], np.float32)
+    else:
+        raise ValueError(what)
+    _check(lib().sacd_debug_tap(ctx, w, int(mode), out.ctypes.data))
+    return out
+
+
+def sacd_set_debug(ctx, on):
+    _check(lib().sacd_set_debug(ctx, 1 if on else 0))
+
+
+def sacd_replay_mask(ctx, mode, mask):
+    if mask is None:
+        _check(lib().sacd_replay_mask(ctx, int(mode), None))
+        return
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    _check(lib().sacd_replay_mask(ctx, int(mode), m.ctypes.data))
+
+
+def sacd_sync(ctx):
+    _check(lib().sacd_sync(ctx))
+
+
+def sacd_profile_enable(ctx, on):
+    _check(lib().sacd_profile_enable(ctx, 1 if on else 0))
+
+
+def sacd_profile_read(ctx):
+    buf = (sacd_kernel_stat * 16)()
+    n = C.c_int32(0)
+    _check(lib().sacd_profile_read(ctx, buf, 16, C.byref(n)))
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n.value, 16))}
+
+
+def sacd_destroy(ctx):
+    if ctx:
+        lib().sacd_destroy(ctx)
+
+
+class SaCD:
+    """Owning wrapper around a context: ``SaCD(dims, idx, vals, rank, init=...)``."""
+
+    def __init__(self, dims, idx, vals, rank, init=None, **kw):
+        self.ctx = sacd_create(dims, idx, vals, rank, init, **kw)
+        self.info = sacd_get_info(self.ctx)
+
+    def mode_step(self, mode, want_count=True):
+        return sacd_mode_step(self.ctx, mode, want_count)
+
+    def iterate(self, iters):
+        sacd_iterate(self.ctx, iters)
+
+    def fit(self):
+        return sacd_fit(self.ctx)
+
+    def factor(self, mode):
+        return sacd_get_factor(self.ctx, mode)
+
+    def factors(self):
+        return [self.factor(n) for n in range(self.info["nmodes"])]
+
+    def set_factor(self, mode, A):
+        sacd_set_factor(self.ctx, mode, A)
+
+    def tap(self, what, mode=0, last_mode=None):
+        return sacd_debug_tap(self.ctx, what, mode, last_mode)
+
+    def set_debug(self, on):
+        sacd_set_debug(self.ctx, on)
+
+    def replay_mask(self, mode, mask):
+        sacd_replay_mask(self.ctx, mode, mask)
+
+    def sync(self):
+        sacd_sync(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            sacd_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
