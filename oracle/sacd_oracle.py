@@ -32,6 +32,8 @@ design notes of the repository):
 * The objective sums over all cells (Eq. 7), so f = ||X||^2 - 2<X, M> + ||M||^2 with M the
   CP model; "fit" (not defined by the paper) is 1 - sqrt(max(f, 0)) / ||X||.
 * Duplicate coordinates are summed (in FP32, in their input order) before anything else.
+* The BF16-gather variant (not in the paper) is defined here as: each gathered factor value is
+  the FP32 factor rounded to the nearest BF16 (ties to even); everything else is unchanged.
 
 Pins (tests/test_oracle_pins.py) tie each function here to something other than itself:
 explicit unfoldings and Khatri-Rao products, finite differences, the exact 1-D decrease, a HALS
@@ -43,6 +45,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
+    "round_bf16",
     "coalesce",
     "csf_order",
     "csf_arrays",
@@ -63,6 +66,16 @@ __all__ = [
     "fit_from_objective",
     "SaCDOracle",
 ]
+
+
+def round_bf16(a):
+    """FP32 values rounded to the nearest BF16 (8-bit significand), ties to even; as FP64.
+
+    BF16 keeps the upper 16 bits of the FP32 encoding: add 0x7FFF plus the lowest kept bit,
+    then clear the low 16 bits (finite inputs only)."""
+    x = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    x = (x + 0x7FFF + ((x >> 16) & 1)) & 0xFFFF0000
+    return x.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 # ----------------------------------------------------------------------------------------
@@ -289,7 +302,7 @@ class SaCDOracle:
     ti^{k-1} (tiprev[n]) and whether the factor has been visited yet (first[n]).
     """
 
-    def __init__(self, dims, idx, vals, init, *, lnorm="fro", fixup="column_gs"):
+    def __init__(self, dims, idx, vals, init, *, lnorm="fro", fixup="column_gs", gather="fp32"):
         self.dims = [int(d) for d in dims]
         self.N = len(self.dims)
         self.idx, self.vals = coalesce(self.dims, idx, vals)
@@ -297,6 +310,7 @@ class SaCDOracle:
         self.R = self.A[0].shape[1]
         self.lnorm = lnorm
         self.fixup = fixup
+        self.gather = gather  # "fp32": gathered factors as they are; "bf16": rounded to BF16
         self.Zprev = [np.zeros((d, self.R)) for d in self.dims]
         self.tiprev = [0.0] * self.N
         self.first = [True] * self.N
@@ -310,7 +324,11 @@ class SaCDOracle:
         taken elsewhere, so that the arithmetic alone can be compared).
         """
         A = self.A[n]
-        M = mttkrp(self.dims, self.idx, self.vals, self.A, n)  # Eq. 9, X_(n)(KRP)
+        if self.gather == "bf16":
+            gathered = [round_bf16(F.astype(np.float32)) if k != n else F for k, F in enumerate(self.A)]
+        else:
+            gathered = self.A
+        M = mttkrp(self.dims, self.idx, self.vals, gathered, n)  # Eq. 9, X_(n)(KRP)
         H = hadamard_of_grams(self.A, n)  # Eq. 10
         G = gradient(A, H, M)  # Eq. 9 / 14
         h = np.diag(H)[None, :]

@@ -349,3 +349,16 @@ def test_pins_catch_planted_mistakes(monkeypatch):
         with pytest.raises(AssertionError):
             test_hand_worked_selection_table()
     del O._orig_mttkrp
+
+
+def test_round_bf16_against_torch_and_hand_values():
+    torch = pytest.importorskip("torch")
+    # hand values: 1 + 2^-8 is a tie between 1 and 1 + 2^-7 -> even (1); 1 + 3*2^-8 -> 1 + 2^-6
+    hand = np.array([1.0, 1.0 + 2**-8, 1.0 + 3 * 2**-8, 1.0 + 2**-8 + 2**-20, 0.0, 3.0e-39], np.float32)
+    want = np.array([1.0, 1.0, 1.0 + 2**-6, 1.0 + 2**-7, 0.0, np.float32(3.0e-39)], np.float64)
+    got = O.round_bf16(hand)
+    np.testing.assert_array_equal(got[:5], want[:5])
+    rng = np.random.default_rng(3)
+    x = (rng.random(100_000) * 10.0 ** rng.integers(-8, 8, 100_000)).astype(np.float32)
+    ref = torch.from_numpy(x).bfloat16().float().numpy().astype(np.float64)
+    np.testing.assert_array_equal(O.round_bf16(x), ref)
