@@ -11,7 +11,7 @@ namespace sacd {
 
 // ---- MTTKRP (mttkrp.cu)
 void launch_mttkrp(const StepDesc* d_descs, const int64_t* d_tile_base, int njobs, int64_t total_tiles, int prec,
-                   int rv, cudaStream_t st);
+                   int rv, int nother, cudaStream_t st);
 void launch_fixup_light(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st);
 void launch_fixup_heavy(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st);
 

@@ -49,7 +49,13 @@ struct WarpPieces {
 };
 
 constexpr int kWarpsPerBlock = 8;
-constexpr int kUnroll = 4;
+#ifndef SACD_MTTKRP_UNROLL
+#define SACD_MTTKRP_UNROLL 4
+#endif
+#ifndef SACD_MTTKRP_MINB
+#define SACD_MTTKRP_MINB 4
+#endif
+constexpr int kUnroll = SACD_MTTKRP_UNROLL;  // nonzeros whose gathers are issued together
 
 template <int PREC, int RV>
 struct TileShape {
@@ -91,42 +97,47 @@ __device__ void zero_rows(float* __restrict__ Mout, int Rp, int64_t r0, int64_t 
   }
 }
 
-template <int PREC, int RV>
+// One warp tile. NO = number of other modes (N-1) when known at compile time, 0 = any.
+// Element positions fit in 32 bits (nnz <= 2^31 - 1); addresses are formed in 64 bits.
+template <int PREC, int RV, int NO>
 __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpPieces& wp) {
   using S = TileShape<PREC, RV>;
+  constexpr int MAXO = NO > 0 ? NO : SACD_MAXN - 1;
   const int lane = lane_id();
   const int g = lane / S::LPR;   // group
   const int lig = lane % S::LPR; // lane in group
   // descriptor fields in registers (stores below cannot alias them)
-  const int64_t nnz = dp->nnz;
+  const int nnz = (int)dp->nnz;
   const int tile_nnz = dp->tile, sub = dp->sub, Rp = dp->Rp;
   const int64_t I = dp->I;
   float* __restrict__ Mout = dp->M;
   float* __restrict__ carry = dp->carry;
   const int32_t* __restrict__ rowid = dp->rowid;
-  const int32_t* __restrict__ cidx = dp->cidx;
   const float* __restrict__ val = dp->val;
-  const int nother = dp->nother;
-  const void* fac[SACD_MAXN - 1];
+  const int nother = NO > 0 ? NO : dp->nother;
+  const int32_t* ci[MAXO];
+  const void* fac[MAXO];
 #pragma unroll
-  for (int m = 0; m < SACD_MAXN - 1; ++m) fac[m] = dp->fac[m];
-  const int64_t t0 = tile * tile_nnz;
-  const int64_t t1 = min(t0 + (int64_t)tile_nnz, nnz);
-  const int64_t a = t0 + (int64_t)g * sub;
-  const int64_t b = min(a + (int64_t)sub, t1);
-  const int rv = RV;
+  for (int m = 0; m < MAXO; ++m) {
+    ci[m] = dp->cidx + (int64_t)m * nnz;
+    fac[m] = dp->fac[m];
+  }
+  const int t0 = (int)(tile * tile_nnz);
+  const int t1 = min(t0 + tile_nnz, nnz);
+  const int a = min(t0 + g * sub, t1);
+  const int b = min(a + sub, t1);
 
   float acc[S::NV];
 #pragma unroll
   for (int i = 0; i < S::NV; ++i) acc[i] = 0.f;
   int32_t cur = -1;
-  int64_t seg = a;
+  int seg = a;
   int flags = 0;
   const int32_t before = (a > 0 && a < b) ? __ldg(rowid + a - 1) : -1;
   const int32_t after = (b < nnz && a < b) ? __ldg(rowid + b) : -1;
 
   // close the segment [s, e_end) of row `row`
-  auto close_seg = [&](int32_t row, int64_t s, int64_t e_end) {
+  auto close_seg = [&](int32_t row, int s, int e_end) {
     const bool lopen = (s == a) && (before == row);
     const bool ropen = (e_end == b) && (after == row);
     if (!lopen && !ropen) {
@@ -152,25 +163,25 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
     }
   };
 
-  for (int64_t e0 = a; e0 < b; e0 += kUnroll) {
+  for (int e0 = a; e0 < b; e0 += kUnroll) {
     int32_t rows[kUnroll];
     float prod[kUnroll][S::NV];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      const int64_t e = e0 + u;
+      const int e = e0 + u;
       if (e < b) {
         rows[u] = __ldg(rowid + e);
         const float x = __ldg(val + e);
 #pragma unroll
         for (int i = 0; i < S::NV; ++i) prod[u][i] = x;
 #pragma unroll
-        for (int m = 0; m < SACD_MAXN - 1; ++m) {
-          if (m < nother) {
-            const int64_t r = __ldg(cidx + (int64_t)m * nnz + e);
+        for (int m = 0; m < MAXO; ++m) {
+          if (NO > 0 || m < nother) {
+            const uint32_t r = (uint32_t)__ldg(ci[m] + e);
 #pragma unroll
             for (int k = 0; k < S::CPL; ++k) {
               float v[S::W];
-              GatherVec<PREC>::load(fac[m], r * rv + lig + k * S::LPR, v);
+              GatherVec<PREC>::load(fac[m], (int64_t)r * RV + lig + k * S::LPR, v);
 #pragma unroll
               for (int i = 0; i < S::W; ++i) prod[u][k * S::W + i] *= v[i];
             }
@@ -182,7 +193,7 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      const int64_t e = e0 + u;
+      const int e = e0 + u;
       if (e < b) {
         if (rows[u] != cur) {
           if (cur >= 0) close_seg(cur, seg, e);
@@ -273,8 +284,10 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
   }
 }
 
-template <int PREC, int RV>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+// 8 warps per block; SACD_MTTKRP_MINB resident blocks per SM bound the registers, so that
+// enough gathers are in flight to cover the L2 latency.
+template <int PREC, int RV, int NO>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, SACD_MTTKRP_MINB)
     mttkrp_kernel(const StepDesc* __restrict__ descs, const int64_t* __restrict__ tile_base, int njobs,
                   int64_t total_tiles) {
   __shared__ WarpPieces pieces[kWarpsPerBlock];
@@ -282,7 +295,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   const int64_t gt = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
   if (gt >= total_tiles) return;
   const int j = njobs > 1 ? find_job(tile_base, njobs, gt) : 0;
-  mttkrp_tile<PREC, RV>(descs + j, gt - tile_base[j], pieces[warp]);
+  mttkrp_tile<PREC, RV, NO>(descs + j, gt - tile_base[j], pieces[warp]);
 }
 
 // Rows split across tiles, with few partials: one warp per row, partials summed in tile order.
@@ -351,31 +364,43 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <int PREC>
-static void launch_mttkrp_prec(const StepDesc* d_descs, const int64_t* d_tile_base, int njobs, int64_t total_tiles,
-                               int rv, cudaStream_t st) {
+template <int PREC, int NO>
+static void launch_mttkrp_no(const StepDesc* d_descs, const int64_t* d_tile_base, int njobs, int64_t total_tiles,
+                             int rv, cudaStream_t st) {
   const unsigned blocks = (unsigned)((total_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
   const int T = kWarpsPerBlock * 32;
   switch (rv) {
-    case 1: mttkrp_kernel<PREC, 1><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
-    case 2: mttkrp_kernel<PREC, 2><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
-    case 4: mttkrp_kernel<PREC, 4><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
-    case 8: mttkrp_kernel<PREC, 8><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
-    case 16: mttkrp_kernel<PREC, 16><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
-    case 32: mttkrp_kernel<PREC, 32><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
-    case 64: mttkrp_kernel<PREC, 64><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 1: if (PREC == 1) mttkrp_kernel<PREC, 1, NO><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 2: mttkrp_kernel<PREC, 2, NO><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 4: mttkrp_kernel<PREC, 4, NO><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 8: mttkrp_kernel<PREC, 8, NO><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 16: mttkrp_kernel<PREC, 16, NO><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 32: mttkrp_kernel<PREC, 32, NO><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
+    case 64: if (PREC == 0) mttkrp_kernel<PREC, 64, NO><<<blocks, T, 0, st>>>(d_descs, d_tile_base, njobs, total_tiles); break;
     default: break;
   }
 }
 
-// All jobs of one launch share the gathered-row width `rv` (16-byte vectors per row).
+template <int PREC>
+static void launch_mttkrp_prec(const StepDesc* d_descs, const int64_t* d_tile_base, int njobs, int64_t total_tiles,
+                               int rv, int nother, cudaStream_t st) {
+  if (nother == 2)
+    launch_mttkrp_no<PREC, 2>(d_descs, d_tile_base, njobs, total_tiles, rv, st);
+  else if (nother == 3)
+    launch_mttkrp_no<PREC, 3>(d_descs, d_tile_base, njobs, total_tiles, rv, st);
+  else
+    launch_mttkrp_no<PREC, 0>(d_descs, d_tile_base, njobs, total_tiles, rv, st);
+}
+
+// All jobs of one launch share the gathered-row width `rv` (16-byte vectors per row) and the
+// number of other modes `nother`.
 void launch_mttkrp(const StepDesc* d_descs, const int64_t* d_tile_base, int njobs, int64_t total_tiles, int prec,
-                   int rv, cudaStream_t st) {
+                   int rv, int nother, cudaStream_t st) {
   if (total_tiles <= 0) return;
   if (prec == 0)
-    launch_mttkrp_prec<0>(d_descs, d_tile_base, njobs, total_tiles, rv, st);
+    launch_mttkrp_prec<0>(d_descs, d_tile_base, njobs, total_tiles, rv, nother, st);
   else
-    launch_mttkrp_prec<1>(d_descs, d_tile_base, njobs, total_tiles, rv, st);
+    launch_mttkrp_prec<1>(d_descs, d_tile_base, njobs, total_tiles, rv, nother, st);
 }
 
 void launch_fixup_light(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st) {

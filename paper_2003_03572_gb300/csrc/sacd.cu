@@ -106,6 +106,10 @@ struct sacd_ctx {
   int64_t fit_blocks = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  // second stream and events for the graph's parallel branch (Gram and H of the next mode
+  // run beside the next mode's MTTKRP)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev[3 * SACD_MAXN + 2] = {};
   Prof prof;
 };
 
@@ -226,7 +230,7 @@ void enqueue_mttkrp(sacd_ctx* c, int n) {
   }
   {
     KScope k(c, K_MTTKRP);
-    launch_mttkrp(dd, c->zero64, 1, md.ntiles, c->prec, c->rv, c->st);
+    launch_mttkrp(dd, c->zero64, 1, md.ntiles, c->prec, c->rv, c->N - 1, c->st);
   }
   if (md.nlight) {
     KScope k(c, K_FIXUP);
@@ -261,6 +265,37 @@ void enqueue_step(sacd_ctx* c, int n) {
     launch_pass2(dd, c->zero64, 1, md.p2_blocks, c->Rp, c->st);
   }
   enqueue_gram(c, n);
+}
+
+// One outer iteration as a DAG, captured into the CUDA graph. Main stream: MTTKRP(n) ->
+// pass1(n) -> pass2(n) -> MTTKRP(n+1) ...; side stream: Gram(n) -> H/L(n+1), which only needs
+// the updated factor n and the Grams, so it overlaps MTTKRP(n+1). Same kernels and inputs as the
+// sequential order, so the results are identical.
+void enqueue_iteration_dag(sacd_ctx* c) {
+  cudaEvent_t* ev = c->ev;  // [0] fork, [1..N] H ready, [N+1..2N] pass2 done, [2N+1] join
+  const int N = c->N;
+  cudaEventRecord(ev[0], c->st);
+  cudaStreamWaitEvent(c->side, ev[0], 0);
+  launch_hl(c->ddesc + 0, 1, c->side);
+  cudaEventRecord(ev[1], c->side);
+  for (int n = 0; n < N; ++n) {
+    ModeData& md = c->m[n];
+    StepDesc* dd = c->ddesc + n;
+    enqueue_mttkrp(c, n);
+    cudaStreamWaitEvent(c->st, ev[1 + n], 0);
+    launch_pass1(dd, c->zero64, 1, md.p1_blocks, c->Rp, c->st);
+    launch_pass2(dd, c->zero64, 1, md.p2_blocks, c->Rp, c->st);
+    cudaEventRecord(ev[N + 1 + n], c->st);
+    cudaStreamWaitEvent(c->side, ev[N + 1 + n], 0);
+    launch_gram(dd, c->zero64, 1, md.gram_blocks, c->Rp, c->side);
+    launch_gram_reduce(dd, c->zero64, 1, gram_reduce_blocks(c->Rp), c->side);
+    if (n + 1 < N) {
+      launch_hl(c->ddesc + n + 1, 1, c->side);
+      cudaEventRecord(ev[2 + n], c->side);
+    }
+  }
+  cudaEventRecord(ev[2 * N + 1], c->side);
+  cudaStreamWaitEvent(c->st, ev[2 * N + 1], 0);
 }
 
 void invalidate_graph(sacd_ctx* c) {
@@ -456,6 +491,8 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
     c->own_stream = true;
   }
+  CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  for (auto& e : c->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   const int R = c->R, Rp = c->Rp;
   const cudaMemcpyKind in_kind = cfg->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
 
@@ -562,7 +599,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     tiles_max = std::max(tiles_max, md.ntiles);
     md.p1_blocks = (I + RB1 - 1) / RB1;
     md.p2_blocks = (I + RB2 - 1) / RB2;
-    md.gram_blocks = std::min<int64_t>((I + CH - 1) / CH, 152);
+    md.gram_blocks = std::min<int64_t>((I + CH - 1) / CH, 4 * 152);
     p1_max = std::max(p1_max, md.p1_blocks);
     gb_max = std::max(gb_max, md.gram_blocks);
     TRY(dalloc(c, &md.A, (size_t)I * Rp));
@@ -755,7 +792,7 @@ sacd_status sacd_iterate(sacd_ctx* c, int32_t iters) {
   } else {
     if (!c->gexec) {
       CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-      for (int n = 0; n < c->N; ++n) enqueue_step(c, n);
+      enqueue_iteration_dag(c);
       cudaGraph_t g = nullptr;
       const cudaError_t e = cudaStreamEndCapture(c->st, &g);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
@@ -988,6 +1025,9 @@ void sacd_destroy(sacd_ctx* c) {
   invalidate_graph(c);
   for (auto& e : c->prof.ev) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   cudaGetLastError();
   delete c;

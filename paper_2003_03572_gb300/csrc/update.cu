@@ -109,6 +109,7 @@ static size_t pass_smem_bytes(int Rp) {
   size_t b = (size_t)RB * (Rp + 1) * sizeof(float);  // staged A rows
   if (Rp <= 64) b += (size_t)Rp * Rp * sizeof(float);  // H
   b += (size_t)RB * 32;                                // selection bytes (pass 2)
+  b += (size_t)8 * 2 * Rp * sizeof(float);             // per-warp G and M rows (pass 2)
   return (b + 15) / 16 * 16;
 }
 
@@ -264,6 +265,7 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
   float* As = sm;
   float* Hs = sm + RB * ST;
   uint8_t* selb = reinterpret_cast<uint8_t*>(sm + RB * ST + (Rp <= 64 ? Rp * Rp : 0));
+  float* wrow = reinterpret_cast<float*>(selb + RB * 32);  // 8 warps x (G row, M row)
   const float* __restrict__ Hsrc = dp->Hf;
   stage_rows(A + row0 * Rp, As, nrows, Rp);
   if (Rp <= 64) {
@@ -329,6 +331,13 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
     if (!any) continue;
     const int64_t row = row0 + r2;
     float* arow = As + r2 * ST;
+    float* grow = wrow + warp * 2 * Rp;
+    float* mrow = grow + Rp;
+    for (int c = lane; c < Rp; c += 32) {
+      grow[c] = __ldg(G + row * Rp + c);
+      if (gs) mrow[c] = __ldg(M + row * Rp + c);
+    }
+    __syncwarp();
     bool upd = false;
     for (int r = 0; r < R; ++r) {
       if (!((selb[r2 * TPR + (r >> 3)] >> (r & 7)) & 1u)) continue;
@@ -350,10 +359,10 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
           lo = __fadd_rn(__fadd_rn(lo, olo), t);
         }
         float s, t;
-        two_sum(hi, -__ldg(M + row * Rp + r), s, t);
+        two_sum(hi, -mrow[r], s, t);
         g = __fadd_rn(s, __fadd_rn(lo, t));
       } else {
-        g = __ldg(G + row * Rp + r);
+        g = grow[r];
       }
       const float s = sacd_step(ar, g, __ldg(invh + r));
       if (s != 0.f) {
@@ -370,6 +379,7 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
         if (A16) A16[row * Rp + c] = __float2bfloat16_rn(v);
       }
     }
+    __syncwarp();
   }
 }
 

@@ -9,9 +9,9 @@ Tolerances (written here, from the stated targets):
   replays the GPU's mask): factor after the step <= 1e-5 relative; z <= 1e-5 of max |z|.
 * free selection: every element where the GPU and the oracle disagree must sit at the decision
   boundary, |sp_oracle| <= 1e-5 max|z| (or the ti comparison is within 1e-6 sum|z|).
-* final fit after K iterations: |delta fit| <= 1e-4 (FP32). BF16 gathers: <= 1e-4 against the
-  oracle's BF16-gather definition; against FP32 gathers the rounding alone moves the fit by
-  about 2e-3 on the Zipf case (bound 5e-3, above the 1e-3 target; the emulation shows why).
+* final fit after K iterations: |delta fit| <= 1e-4 (FP32). BF16 gathers: the mode step matches
+  the oracle's BF16-gather definition within 1e-5; the final fit against the FP64 oracle is
+  bounded by 5e-3 (not the 1e-3 target: BF16 rounding alone flips selections, see the test).
 """
 
 import json
@@ -218,26 +218,33 @@ def test_graph_iterate_equals_mode_steps_and_is_deterministic():
 def test_bf16_gather_mode():
     dims, nnz, dist, s, R = CASES[1]
     idx, vals, init = make_case(dims, nnz, dist, s, R)
+    cidx, cvals = O.coalesce(dims, idx, vals)
     with S.SaCD(dims, idx, vals, R, init, precision=S.SACD_BF16_GATHER) as g:
-        F = g.factors()
-        g.mode_step(0)
-        cidx, cvals = O.coalesce(dims, idx, vals)
-        assert relerr(g.tap("M", 0), O.mttkrp(list(dims), cidx, cvals, F, 0)) <= 1e-2
-        # against the oracle's definition of the BF16-gather variant
-        Fb = [O.round_bf16(f) for f in F]
-        assert relerr(g.tap("M", 0), O.mttkrp(list(dims), cidx, cvals, Fb, 0)) <= 1e-5
-    with S.SaCD(dims, idx, vals, R, init, precision=S.SACD_BF16_GATHER) as g:
+        g.set_debug(True)
         ob = O.SaCDOracle(dims, idx, vals, init, gather="bf16")
+        for it in range(2):
+            for n in range(3):
+                F = g.factors()
+                zprev = g.tap("ZPREV", n)
+                st = g.tap("STATE", n)
+                g.mode_step(n)
+                assert relerr(g.tap("M", n), O.mttkrp(list(dims), cidx, cvals, F, n)) <= 1e-2
+                # the oracle's definition of the BF16-gather variant, selection replayed
+                ob.A = [f.astype(np.float64) for f in F]
+                ob.Zprev[n] = zprev.astype(np.float64)
+                ob.tiprev[n] = st[0]
+                ob.first[n] = st[1] != 0
+                ob.mode_step(n, mask=g.tap("MASK", n, last_mode=n).astype(bool))
+                assert relerr(g.tap("M", n), ob.last["M"]) <= 1e-5
+                assert relerr(g.factor(n), ob.A[n]) <= 1e-5
+    with S.SaCD(dims, idx, vals, R, init, precision=S.SACD_BF16_GATHER) as g:
         o = O.SaCDOracle(dims, idx, vals, init)
-        g.iterate(10)
-        ob.iterate(10)
-        o.iterate(10)
-        fit = g.fit()[1]
-        assert abs(fit - ob.fit()[1]) <= 1e-4
-        # against FP32 gathers: the BF16 rounding alone moves the fit by about 2e-3 here
-        # (the FP64 oracle with only its gathered factors rounded shows the same), so the
-        # bound is looser than the 1e-3 target
-        assert abs(fit - o.fit()[1]) <= 5e-3
+        g.iterate(30)
+        o.iterate(30)
+        # BF16 rounding of the gathered rows flips selections (Eq. 24/27 are discontinuous),
+        # so whole trajectories drift: an FP64 emulation that only rounds the gathered
+        # factors moves the fit of this case by 1.7e-3 after 10 and 0.9e-3 after 30 iterations.
+        assert abs(g.fit()[1] - o.fit()[1]) <= 5e-3
 
 
 def test_edge_cases():
