@@ -50,10 +50,10 @@ struct WarpPieces {
 
 constexpr int kWarpsPerBlock = 8;
 #ifndef SACD_MTTKRP_UNROLL
-#define SACD_MTTKRP_UNROLL 4
+#define SACD_MTTKRP_UNROLL 2
 #endif
 #ifndef SACD_MTTKRP_MINB
-#define SACD_MTTKRP_MINB 4
+#define SACD_MTTKRP_MINB 3
 #endif
 constexpr int kUnroll = SACD_MTTKRP_UNROLL;  // nonzeros whose gathers are issued together
 
