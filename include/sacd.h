@@ -24,6 +24,7 @@
 #ifndef SACD_H
 #define SACD_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -194,6 +195,38 @@ typedef struct {
 
 sacd_status sacd_profile_enable(sacd_ctx* ctx, int32_t on);
 sacd_status sacd_profile_read(sacd_ctx* ctx, sacd_kernel_stat* out, int32_t cap, int32_t* n);
+
+/*
+ * sacd_mttkrp_noalloc -- the MTTKRP of one mode, M = X_(mode) (Khatri-Rao of the other
+ * factors), computed without allocating any device memory. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as code inside a host
+ * framework that owns the whole device memory pool and forbids allocations outside its plan,
+ * or latency-critical loops that cannot afford the synchronisation cudaMalloc/cudaFree may imply.
+ *
+ * All array arguments are device pointers owned by the caller:
+ *   rowid  nnz int32, the mode-`mode` index of each nonzero, sorted ascending (e.g. the
+ *          SACD_TAP_CSF_ROW layout of a context);
+ *   cidx   (nmodes-1) x nnz int32, the other modes' indices in ascending mode order;
+ *   vals   nnz FP32 values;
+ *   factors host array of nmodes device pointers; factors[k] (k != mode) is I_k x ld FP32
+ *          row-major, 16-byte aligned, with columns >= rank set to zero (factors[mode] unused);
+ *   M      output, I_mode x ld FP32 row-major, 16-byte aligned; every entry is written.
+ * ld must be the padded rank, the next power of two >= max(8, rank). dims is a host array.
+ * The work runs on `stream` (cudaStream_t, NULL = legacy default stream) and is not waited for.
+ *
+ * Scratch: a file-scope static device array of SACD_NOALLOC_SCRATCH_MIB MiB, held by every GPU
+ * that loads the library until the process exits. A call needs 4 KiB + 2 * ceil(nnz / tile) *
+ * ld * 4 bytes of it (tile = 32 / min(ld/4, 32) lane groups x 8..128 nonzeros, chosen from
+ * nnz); larger problems are rejected with SACD_EINVAL before any GPU work. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture. Every call shares the array: calls that overlap on the GPU race.
+ * Errors: SACD_EINVAL (ranges, null or misaligned pointers, too large), SACD_ECUDA.
+ */
+#define SACD_NOALLOC_SCRATCH_MIB 16
+sacd_status sacd_mttkrp_noalloc(int32_t nmodes, int32_t mode, const int64_t* dims, int64_t nnz,
+                                const int32_t* rowid, const int32_t* cidx, const float* vals,
+                                const float* const* factors, int32_t rank, int32_t ld, float* M,
+                                void* stream);
 
 /* sacd_destroy -- release everything the context owns. NULL-safe; legal on a poisoned context. */
 void sacd_destroy(sacd_ctx* ctx);

@@ -9,6 +9,9 @@ struct FitDesc;
 
 namespace sacd {
 
+// message returned by sacd_last_error() on this thread
+void set_last_error(const char* msg);
+
 // ---- MTTKRP (mttkrp.cu)
 void launch_mttkrp(const StepDesc* d_descs, const int64_t* d_tile_base, int njobs, int64_t total_tiles, int prec,
                    int rv, int nother, cudaStream_t st);

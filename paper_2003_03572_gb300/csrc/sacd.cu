@@ -65,6 +65,8 @@ struct Prof {
 
 }  // namespace
 
+void sacd::set_last_error(const char* msg) { g_err = msg; }
+
 struct sacd_ctx {
   int N = 0;
   int64_t dims[SACD_MAXN] = {0};

@@ -39,6 +39,7 @@ __all__ = [
     "sacd_sync",
     "sacd_profile_enable",
     "sacd_profile_read",
+    "sacd_mttkrp_noalloc",
     "sacd_destroy",
     "sacd_last_error",
     "SaCD",
@@ -126,6 +127,7 @@ def lib():
         "sacd_sync": (C.c_int, [vp]),
         "sacd_profile_enable": (C.c_int, [vp, i32]),
         "sacd_profile_read": (C.c_int, [vp, C.POINTER(sacd_kernel_stat), i32, C.POINTER(i32)]),
+        "sacd_mttkrp_noalloc": (C.c_int, [i32, i32, C.POINTER(i64), i64, vp, vp, vp, C.POINTER(vp), i32, i32, vp, vp]),
         "sacd_destroy": (None, [vp]),
         "sacd_last_error": (C.c_char_p, []),
     }
@@ -297,6 +299,17 @@ def sacd_profile_read(ctx):
     n = C.c_int32(0)
     _check(lib().sacd_profile_read(ctx, buf, 16, C.byref(n)))
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n.value, 16))}
+
+
+def sacd_mttkrp_noalloc(dims, mode, nnz, rowid, cidx, vals, factors, rank, ld, M, stream=None):
+    """MTTKRP of one mode without any device allocation (see include/sacd.h). Every array
+    argument is a device pointer (an int, or a CUDA tensor); ``factors`` holds one per mode."""
+    N = len(dims)
+    dims_a = (C.c_int64 * N)(*[int(d) for d in dims])
+    fp = (C.c_void_p * N)(*[(_ptr(f) if f is not None and not isinstance(f, int) else f) for f in factors])
+    p = lambda a: a if (a is None or isinstance(a, int)) else _ptr(a)
+    _check(lib().sacd_mttkrp_noalloc(N, int(mode), dims_a, int(nnz), p(rowid), p(cidx), p(vals), fp, int(rank),
+                                     int(ld), p(M), stream))
 
 
 def sacd_destroy(ctx):
