@@ -365,6 +365,79 @@ def ours_arm(args):
     return 0
 
 
+def _gen_job(w):
+    from paper_2003_03572_gb300 import synth
+
+    idx, vals = synth.sparse_tensor(w.dims, w.nnz, dist=w.dist, zipf_s=w.zipf_s, values=w.values, seed=w.seed)
+    return idx, vals, synth.init_factors(w.dims, w.rank, w.seed)
+
+
+def batched_arm(args):
+    """Many small independent jobs: one batched launch set per mode step (CUDA graph) against
+    the same jobs solved one at a time, each from its own context, on the same GPU."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import numpy as np
+    import torch
+
+    from paper_2003_03572_gb300 import sacd as S
+    from paper_2003_03572_gb300 import synth
+
+    ws = synth.batched_workloads(args.jobs)
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4), mp_context=mp.get_context("spawn")) as ex:
+        data = list(ex.map(_gen_job, ws, chunksize=8))
+    torch.cuda.init()
+    stream = torch.cuda.Stream()
+    specs = [dict(dims=w.dims, idx=d[0], vals=d[1], rank=w.rank, init=d[2]) for w, d in zip(ws, data)]
+    iters = ws[0].iters
+    nnz_total = sum(w.nnz for w in ws)
+    mode_steps = sum(w.nmodes for w in ws) * iters
+    # batched
+    b = S.SaCDBatch(specs, stream=stream.cuda_stream)
+    b.iterate(1)  # graph capture and warm-up
+    torch.cuda.synchronize()
+    del b
+    times_b = []
+    fits_b = None
+    for rep in range(args.e2e_reps):
+        b = S.SaCDBatch(specs, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.iterate(iters)
+        obj, fits_b = b.fit()
+        times_b.append(time.perf_counter() - t0)
+        b.close()
+    # one at a time (same contexts, same arithmetic)
+    ctxs = [S.SaCD(sp["dims"], sp["idx"], sp["vals"], sp["rank"], sp["init"], stream=stream.cuda_stream)
+            for sp in specs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fits_1 = []
+    for g in ctxs:
+        g.iterate(iters)
+        fits_1.append(g.fit()[1])
+    t1 = time.perf_counter() - t0
+    for g in ctxs:
+        g.close()
+    tb = statistics.median(times_b)
+    line = {
+        "metric": "batched SaCD jobs/s",
+        "value": len(ws) / tb,
+        "unit": "jobs/s",
+        "one_at_a_time": len(ws) / t1,
+        "speedup": t1 / tb,
+        "mode_steps_per_s": mode_steps / tb,
+        "same_final_fit": bool(np.array_equal(np.asarray(fits_b), np.asarray(fits_1))),
+        "config": {"workload": f"batched {len(ws)} jobs: dims U[200,5000]xU[200,5000]xU[20,200], nnz U[10k,500k] "
+                               f"Zipf(1.1), R in {{8,16,32}}, FP32, {iters} iterations", "nnz_total": nnz_total},
+        "seconds_batched": tb,
+        "seconds_one_at_a_time": t1,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,6 +449,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true", help="skip the end-to-end and CPU legs (profiling)")
     ap.add_argument("--cpu-baseline-child", action="store_true")
+    ap.add_argument("--batched", action="store_true", help="the many-small-jobs workload (batched vs one at a time)")
+    ap.add_argument("--jobs", type=int, default=512)
     args = ap.parse_args()
     if args.cpu_baseline_child:
         cpu_baseline_child(args.workload, args.steps)
@@ -384,6 +459,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if args.batched:
+        return batched_arm(args)
     return ours_arm(args)
 
 

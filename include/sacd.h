@@ -228,6 +228,25 @@ sacd_status sacd_mttkrp_noalloc(int32_t nmodes, int32_t mode, const int64_t* dim
                                 const float* const* factors, int32_t rank, int32_t ld, float* M,
                                 void* stream);
 
+/*
+ * Batches (not in the paper; the batched workload of many small tensors). A batch owns `njobs`
+ * independent contexts, created from cfgs[0..njobs-1] (their `stream` fields are ignored: all
+ * jobs run on the batch's stream, the caller's or one the batch creates). sacd_batch_iterate runs
+ * `iters` outer iterations of every job (each job's modes 0..N_j-1 in order), launching each
+ * kernel of a mode step once for all jobs that have that mode (the MTTKRP and Gram once per
+ * row-width class), from a CUDA graph. A job's results are bit-identical to running its context
+ * alone. sacd_batch_fit evaluates every job's objective and fit (arrays of njobs; NULL allowed)
+ * and waits. sacd_batch_job lends a job's context (for sacd_get_factor, taps, ...); the batch
+ * keeps owning it. Errors: SACD_EINVAL, SACD_ENOMEM, SACD_ECUDA, SACD_ESTATE (poisoned batch,
+ * a job with a pending replay mask).
+ */
+typedef struct sacd_batch sacd_batch;
+sacd_status sacd_batch_create(const sacd_config* cfgs, int32_t njobs, void* stream, sacd_batch** out);
+sacd_status sacd_batch_iterate(sacd_batch* b, int32_t iters);
+sacd_status sacd_batch_fit(sacd_batch* b, double* objective, double* fit);
+sacd_status sacd_batch_job(sacd_batch* b, int32_t job, sacd_ctx** ctx_out);
+void sacd_batch_destroy(sacd_batch* b);
+
 /* sacd_destroy -- release everything the context owns. NULL-safe; legal on a poisoned context. */
 void sacd_destroy(sacd_ctx* ctx);
 

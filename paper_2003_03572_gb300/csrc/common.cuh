@@ -44,8 +44,11 @@ struct StepDesc {
   float* carry;          // ntiles x 2 x Rp open-segment partials
   const int4* split_light;  // {row, first tile, last tile, 0}: rows straddling tiles, few partials
   int64_t nsplit_light;
-  const int4* split_heavy;  // same, many partials
+  const int4* split_heavy;  // {row, first chunk, chunk count, 0}: rows with many partials
   int64_t nsplit_heavy;
+  const int4* fix_chunks;   // {row, first tile, first partial, count} chunks of heavy rows
+  int64_t nfix_chunks;
+  float* carry2;            // nfix_chunks x Rp chunk sums
   // ---- update of factor n
   float* A;              // I x Rp FP32 master
   __nv_bfloat16* A16;    // I x Rp BF16 mirror (or null)

@@ -16,6 +16,8 @@ void set_last_error(const char* msg);
 void launch_mttkrp(const StepDesc* d_descs, const int64_t* d_tile_base, int njobs, int64_t total_tiles, int prec,
                    int rv, int nother, cudaStream_t st);
 void launch_fixup_light(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st);
+void launch_fixup_chunks(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st);
+constexpr int kFixChunk = 128;  // partials per level-1 chunk of a heavy split row
 void launch_fixup_heavy(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st);
 
 // ---- update path (update.cu)
@@ -24,16 +26,17 @@ int rows_per_block_pass1(int Rp);
 int rows_per_block_pass2(int Rp);
 __host__ __device__ int gram_chunk_rows(int Rp);
 void launch_hl(const StepDesc* d_descs, int njobs, cudaStream_t st);
-void launch_pass1(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+size_t pass_smem_bytes(int Rp);  // dynamic shared memory of pass1/pass2 for padded rank Rp
+void launch_pass1(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, size_t smem,
                   cudaStream_t st);
-void launch_pass2(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+void launch_pass2(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, size_t smem,
                   cudaStream_t st);
 void launch_gram(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
                  cudaStream_t st);
 int gram_reduce_blocks(int Rp);
 void launch_gram_reduce(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks,
                         cudaStream_t st);
-void launch_fit(const FitDesc* d_fit, int64_t blocks, cudaStream_t st);
+void launch_fit(const FitDesc* d_fit, const int64_t* d_base, int njobs, int64_t total_blocks, cudaStream_t st);
 void launch_to_bf16(const float* src, void* dst, int64_t n, cudaStream_t st);
 void launch_check_factor(const float* A, int64_t rows, int R, int Rp, unsigned int* bad, cudaStream_t st);
 

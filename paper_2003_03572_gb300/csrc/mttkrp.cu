@@ -320,33 +320,31 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Rows split across many tiles: one block per row; threads take partials strided, then a
-// fixed-shape tree in shared memory.
-__global__ void __launch_bounds__(256)
-    fixup_heavy_kernel(const StepDesc* __restrict__ descs, const int64_t* __restrict__ item_base, int njobs,
-                       int64_t total) {
-  __shared__ float4 red[256];
-  const int64_t gi = blockIdx.x;
-  if (gi >= total) return;
-  const int j = njobs > 1 ? find_job(item_base, njobs, gi) : 0;
-  const StepDesc& d = descs[j];
-  const int4 s = d.split_heavy[gi - item_base[j]];
-  const int nvec = d.Rp >> 2;
-  const float4* carry = reinterpret_cast<const float4*>(d.carry);
-  float4* Mrow = reinterpret_cast<float4*>(d.M + (int64_t)s.x * d.Rp);
-  const int64_t P = (int64_t)s.z - s.y + 1;  // partials: slot 1 of tile s.y, slot 0 of the rest
+// Rows split across many tiles, two levels. Level 1: one block per chunk of at most
+// kFixChunk partials of one row ({row, first tile, first partial, count}); threads take partials
+// strided, then a fixed-shape tree in shared memory; the chunk sum goes to carry2. Level 2: one
+// block per row sums its chunks' sums the same way into M. Partial k of a row whose first tile
+// is tf is slot 1 of tile tf for k = 0 and slot 0 of tile tf + k otherwise.
+__device__ __forceinline__ void block_tree_sum(const float4* __restrict__ src, int64_t stride_vec, int64_t P,
+                                               int nvec, float4* __restrict__ dst, float4* red,
+                                               const int64_t* __restrict__ idx_of /* nullable */,
+                                               int64_t tf, int64_t k0) {
   for (int c0 = 0; c0 < nvec; c0 += 256) {
-    const int cw = min(256, nvec - c0);      // vectors handled in this pass
-    const int lanes = 256 / cw;              // partial lanes (cw divides 256: powers of two)
+    const int cw = min(256, nvec - c0);  // vectors handled in this pass (cw divides 256)
+    const int lanes = 256 / cw;
     const int c = c0 + (threadIdx.x % cw);
     const int pl = threadIdx.x / cw;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (pl < lanes) {
-      for (int64_t p = pl; p < P; p += lanes) {
-        const int64_t t = s.y + p;
-        const float4 v = carry[(t * 2 + (p == 0 ? 1 : 0)) * nvec + c];
-        acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    for (int64_t p = pl; p < P; p += lanes) {
+      int64_t off;
+      if (idx_of == nullptr) {
+        const int64_t k = k0 + p;
+        off = ((tf + k) * 2 + (k == 0 ? 1 : 0)) * stride_vec;
+      } else {
+        off = (idx_of[0] + p) * stride_vec;
       }
+      const float4 v = src[off + c];
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -359,9 +357,39 @@ __global__ void __launch_bounds__(256)
       }
       __syncthreads();
     }
-    if (pl == 0) Mrow[c] = red[threadIdx.x];
+    if (pl == 0) dst[c] = red[threadIdx.x];
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(256)
+    fixup_chunk_kernel(const StepDesc* __restrict__ descs, const int64_t* __restrict__ item_base, int njobs,
+                       int64_t total) {
+  __shared__ float4 red[256];
+  const int64_t gi = blockIdx.x;
+  if (gi >= total) return;
+  const int j = njobs > 1 ? find_job(item_base, njobs, gi) : 0;
+  const StepDesc* __restrict__ dp = descs + j;
+  const int64_t li = gi - item_base[j];
+  const int4 it = dp->fix_chunks[li];  // {row (unused here), first tile, first partial, count}
+  const int nvec = dp->Rp >> 2;
+  block_tree_sum(reinterpret_cast<const float4*>(dp->carry), nvec, it.w, nvec,
+                 reinterpret_cast<float4*>(dp->carry2) + li * nvec, red, nullptr, it.y, it.z);
+}
+
+__global__ void __launch_bounds__(256)
+    fixup_heavy_kernel(const StepDesc* __restrict__ descs, const int64_t* __restrict__ item_base, int njobs,
+                       int64_t total) {
+  __shared__ float4 red[256];
+  const int64_t gi = blockIdx.x;
+  if (gi >= total) return;
+  const int j = njobs > 1 ? find_job(item_base, njobs, gi) : 0;
+  const StepDesc* __restrict__ dp = descs + j;
+  const int4 s = dp->split_heavy[gi - item_base[j]];  // {row, first chunk, chunk count, 0}
+  const int nvec = dp->Rp >> 2;
+  const int64_t first = s.y;
+  block_tree_sum(reinterpret_cast<const float4*>(dp->carry2), nvec, s.z, nvec,
+                 reinterpret_cast<float4*>(dp->M + (int64_t)s.x * dp->Rp), red, &first, 0, 0);
 }
 
 template <int PREC, int NO>
@@ -407,6 +435,11 @@ void launch_fixup_light(const StepDesc* d_descs, const int64_t* d_base, int njob
   if (total <= 0) return;
   const int64_t blocks = (total * 32 + 255) / 256;
   fixup_light_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_descs, d_base, njobs, total);
+}
+
+void launch_fixup_chunks(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st) {
+  if (total <= 0) return;
+  fixup_chunk_kernel<<<(unsigned)total, 256, 0, st>>>(d_descs, d_base, njobs, total);
 }
 
 void launch_fixup_heavy(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st) {

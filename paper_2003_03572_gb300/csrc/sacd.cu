@@ -44,6 +44,8 @@ struct ModeData {
   int64_t nlight = 0;
   int4* split_heavy = nullptr;
   int64_t nheavy = 0;
+  int4* chunks = nullptr;
+  int64_t nchunks = 0;
   // state
   float* A = nullptr;
   __nv_bfloat16* A16 = nullptr;
@@ -89,6 +91,7 @@ struct sacd_ctx {
   uint8_t* mask = nullptr;
   uint8_t* replay = nullptr;
   float* carry = nullptr;
+  float* carry2 = nullptr;
   double* gpart = nullptr;
   double* H = nullptr;
   float* Hf = nullptr;
@@ -105,6 +108,7 @@ struct sacd_ctx {
   FitDesc* dfit = nullptr;
   double* fitpart = nullptr;
   double* fitout = nullptr;
+  int64_t* fitbase = nullptr;  // {0, fit_blocks}
   int64_t fit_blocks = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -240,6 +244,7 @@ void enqueue_mttkrp(sacd_ctx* c, int n) {
   }
   if (md.nheavy) {
     KScope k(c, K_FIXUP);
+    launch_fixup_chunks(dd, c->zero64, 1, md.nchunks, c->st);
     launch_fixup_heavy(dd, c->zero64, 1, md.nheavy, c->st);
   }
 }
@@ -260,11 +265,11 @@ void enqueue_step(sacd_ctx* c, int n) {
   enqueue_mttkrp(c, n);
   {
     KScope k(c, K_PASS1);
-    launch_pass1(dd, c->zero64, 1, md.p1_blocks, c->Rp, c->st);
+    launch_pass1(dd, c->zero64, 1, md.p1_blocks, pass_smem_bytes(c->Rp), c->st);
   }
   {
     KScope k(c, K_PASS2);
-    launch_pass2(dd, c->zero64, 1, md.p2_blocks, c->Rp, c->st);
+    launch_pass2(dd, c->zero64, 1, md.p2_blocks, pass_smem_bytes(c->Rp), c->st);
   }
   enqueue_gram(c, n);
 }
@@ -285,8 +290,8 @@ void enqueue_iteration_dag(sacd_ctx* c) {
     StepDesc* dd = c->ddesc + n;
     enqueue_mttkrp(c, n);
     cudaStreamWaitEvent(c->st, ev[1 + n], 0);
-    launch_pass1(dd, c->zero64, 1, md.p1_blocks, c->Rp, c->st);
-    launch_pass2(dd, c->zero64, 1, md.p2_blocks, c->Rp, c->st);
+    launch_pass1(dd, c->zero64, 1, md.p1_blocks, pass_smem_bytes(c->Rp), c->st);
+    launch_pass2(dd, c->zero64, 1, md.p2_blocks, pass_smem_bytes(c->Rp), c->st);
     cudaEventRecord(ev[N + 1 + n], c->st);
     cudaStreamWaitEvent(c->side, ev[N + 1 + n], 0);
     launch_gram(dd, c->zero64, 1, md.gram_blocks, c->Rp, c->side);
@@ -429,12 +434,26 @@ sacd_status build_mode(sacd_ctx* c, TmpAllocs& T, SortBufs& B, int n, const int3
       std::vector<int4> h(h_tot);
       CK(cudaMemcpyAsync(h.data(), lst, sizeof(int4) * h_tot, cudaMemcpyDeviceToHost, c->st));
       CK(cudaStreamSynchronize(c->st));
-      std::vector<int4> light, heavy;
-      for (const int4& s : h) ((s.z - s.y + 1) <= 16 ? light : heavy).push_back(s);
+      std::vector<int4> light, heavy, chunks;
+      for (const int4& s : h) {
+        const int64_t P = (int64_t)s.z - s.y + 1;  // partials of the row
+        if (P <= 16) {
+          light.push_back(s);
+        } else {
+          const int first = (int)chunks.size();
+          for (int64_t k0 = 0; k0 < P; k0 += kFixChunk)
+            chunks.push_back(make_int4(s.x, s.y, (int)k0, (int)std::min<int64_t>(kFixChunk, P - k0)));
+          heavy.push_back(make_int4(s.x, first, (int)chunks.size() - first, 0));
+        }
+      }
       md.nlight = (int64_t)light.size();
       md.nheavy = (int64_t)heavy.size();
+      md.nchunks = (int64_t)chunks.size();
       TRY(dalloc(c, &md.split_light, light.size()));
       TRY(dalloc(c, &md.split_heavy, heavy.size()));
+      TRY(dalloc(c, &md.chunks, chunks.size()));
+      if (!chunks.empty())
+        CK(cudaMemcpyAsync(md.chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice, c->st));
       if (!light.empty())
         CK(cudaMemcpyAsync(md.split_light, light.data(), sizeof(int4) * light.size(), cudaMemcpyHostToDevice,
                            c->st));
@@ -591,7 +610,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     TRY(build_mode(c, T, B, n, uidx, uvals));
   }
   // ---- factors and state
-  int64_t Imax = 0, tiles_max = 0, p1_max = 0, gb_max = 0;
+  int64_t Imax = 0, tiles_max = 0, p1_max = 0, gb_max = 0, chunks_max = 0;
   const int RB1 = rows_per_block_pass1(Rp), RB2 = rows_per_block_pass2(Rp);
   const int CH = gram_chunk_rows(Rp);
   for (int n = 0; n < N; ++n) {
@@ -599,6 +618,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     const int64_t I = md.I;
     Imax = std::max(Imax, I);
     tiles_max = std::max(tiles_max, md.ntiles);
+    chunks_max = std::max(chunks_max, md.nchunks);
     md.p1_blocks = (I + RB1 - 1) / RB1;
     md.p2_blocks = (I + RB2 - 1) / RB2;
     md.gram_blocks = std::min<int64_t>((I + CH - 1) / CH, 4 * 152);
@@ -647,6 +667,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
   TRY(dalloc(c, &c->replay, (size_t)Imax * Rp));
   TRY(dalloc(c, &c->carry, (size_t)std::max<int64_t>(tiles_max, 1) * 2 * Rp));
   TRY(dalloc(c, &c->gpart, (size_t)gb_max * Rp * Rp));
+  TRY(dalloc(c, &c->carry2, (size_t)std::max<int64_t>(chunks_max, 1) * Rp));
   TRY(dalloc(c, &c->H, (size_t)Rp * Rp));
   TRY(dalloc(c, &c->Hf, (size_t)Rp * Rp));
   TRY(dalloc(c, &c->invh, Rp));
@@ -685,6 +706,9 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     d.nsplit_light = md.nlight;
     d.split_heavy = md.split_heavy;
     d.nsplit_heavy = md.nheavy;
+    d.fix_chunks = md.chunks;
+    d.nfix_chunks = md.nchunks;
+    d.carry2 = c->carry2;
     d.A = md.A;
     d.A16 = md.A16;
     d.G = c->G;
@@ -717,6 +741,12 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     TRY(dalloc(c, &c->fitpart, c->fit_blocks));
     TRY(dalloc(c, &c->fitout, 4));
     TRY(dalloc(c, &c->dfit, 1));
+    TRY(dalloc(c, &c->fitbase, 2));
+    {
+      const int64_t fb[2] = {0, c->fit_blocks};
+      CK(cudaMemcpyAsync(c->fitbase, fb, sizeof(fb), cudaMemcpyHostToDevice, c->st));
+      CK(cudaStreamSynchronize(c->st));
+    }
     FitDesc& f = c->hfit;
     memset(&f, 0, sizeof(f));
     f.A = c->m[L].A;
@@ -816,7 +846,7 @@ sacd_status sacd_fit(sacd_ctx* c, double* objective, double* fit) {
   }
   {
     KScope k(c, K_FIT);
-    launch_fit(c->dfit, c->fit_blocks, c->st);
+    launch_fit(c->dfit, c->fitbase, 1, c->fit_blocks, c->st);
   }
   double out[4];
   CK(cudaMemcpyAsync(out, c->fitout, sizeof(out), cudaMemcpyDeviceToHost, c->st));
@@ -1036,5 +1066,314 @@ void sacd_destroy(sacd_ctx* c) {
 }
 
 const char* sacd_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+// ==========================================================================================
+// Batches: many independent contexts stepped together. Every kernel of a mode step is launched
+// once for all the jobs that have that mode (descriptor arrays + per-job prefix sums of the
+// work items); the MTTKRP and the Gram, which are specialised on the row width, are launched
+// once per width class. Each job's arithmetic is exactly what its own context would do, so a
+// job's results are bit-identical alone and in any mix.
+namespace {
+
+struct PlanClass {
+  int rv = 0, nother = 0, Rp = 0, prec = 0;
+  int njobs = 0;
+  StepDesc* d_descs = nullptr;
+  int64_t* d_tile_base = nullptr;
+  int64_t tiles = 0;
+  int64_t* d_gram_base = nullptr;
+  int64_t gram_blocks = 0;
+};
+
+struct PlanMode {
+  int njobs = 0;
+  std::vector<sacd_ctx*> jobs;
+  StepDesc* d_descs = nullptr;
+  int64_t *d_light = nullptr, *d_chunk = nullptr, *d_heavy = nullptr, *d_p1 = nullptr, *d_p2 = nullptr,
+          *d_gr = nullptr;
+  int64_t light = 0, chunk = 0, heavy = 0, p1 = 0, p2 = 0, gr = 0;
+  size_t smem = 0;
+  std::vector<PlanClass> classes;
+  std::vector<sacd_ctx*> empty_jobs;  // no nonzeros: M is zeroed instead of an MTTKRP
+};
+
+struct BatchPlan {
+  int maxN = 0;
+  int njobs = 0;
+  PlanMode modes[SACD_MAXN];
+  FitDesc* d_fit = nullptr;
+  int64_t* d_fit_base = nullptr;
+  int64_t fit_blocks = 0;
+  double* d_fit_out = nullptr;  // njobs x 4
+  std::vector<void*> allocs;
+
+  template <typename T>
+  sacd_status alloc_copy(T** dst, const std::vector<T>& src, cudaStream_t st) {
+    void* q = nullptr;
+    const size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SACD_ENOMEM, "cudaMalloc of a batch plan array failed");
+    }
+    allocs.push_back(q);
+    *dst = reinterpret_cast<T*>(q);
+    if (!src.empty() && cudaMemcpyAsync(q, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return fail(SACD_ECUDA, "copy of a batch plan array failed");
+    return SACD_OK;
+  }
+
+  void release() {
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+  }
+
+  static std::vector<int64_t> prefix(const std::vector<int64_t>& counts) {
+    std::vector<int64_t> b(counts.size() + 1, 0);
+    for (size_t i = 0; i < counts.size(); ++i) b[i + 1] = b[i] + counts[i];
+    return b;
+  }
+
+  sacd_status build(const std::vector<sacd_ctx*>& jobs, cudaStream_t st) {
+    njobs = (int)jobs.size();
+    maxN = 0;
+    for (sacd_ctx* c : jobs) maxN = std::max(maxN, c->N);
+    for (int n = 0; n < maxN; ++n) {
+      PlanMode& pm = modes[n];
+      pm = PlanMode();
+      std::vector<StepDesc> descs;
+      std::vector<int64_t> light, chunk, heavy, p1, p2, gr;
+      for (sacd_ctx* c : jobs) {
+        if (n >= c->N) continue;
+        pm.jobs.push_back(c);
+        descs.push_back(c->hdesc[n]);
+        const ModeData& md = c->m[n];
+        light.push_back(md.nlight);
+        chunk.push_back(md.nchunks);
+        heavy.push_back(md.nheavy);
+        p1.push_back(md.p1_blocks);
+        p2.push_back(md.p2_blocks);
+        gr.push_back(gram_reduce_blocks(c->Rp));
+        pm.smem = std::max(pm.smem, pass_smem_bytes(c->Rp));
+        if (c->nnz == 0) pm.empty_jobs.push_back(c);
+      }
+      pm.njobs = (int)pm.jobs.size();
+      if (!pm.njobs) continue;
+      auto tot = [](const std::vector<int64_t>& v) { int64_t s = 0; for (auto x : v) s += x; return s; };
+      pm.light = tot(light); pm.chunk = tot(chunk); pm.heavy = tot(heavy);
+      pm.p1 = tot(p1); pm.p2 = tot(p2); pm.gr = tot(gr);
+      TRY(alloc_copy(&pm.d_descs, descs, st));
+      TRY(alloc_copy(&pm.d_light, prefix(light), st));
+      TRY(alloc_copy(&pm.d_chunk, prefix(chunk), st));
+      TRY(alloc_copy(&pm.d_heavy, prefix(heavy), st));
+      TRY(alloc_copy(&pm.d_p1, prefix(p1), st));
+      TRY(alloc_copy(&pm.d_p2, prefix(p2), st));
+      TRY(alloc_copy(&pm.d_gr, prefix(gr), st));
+      // width classes for the MTTKRP (rv, number of other modes, precision) and the Gram (Rp)
+      std::vector<std::vector<sacd_ctx*>> groups;
+      for (sacd_ctx* c : pm.jobs) {
+        bool placed = false;
+        for (auto& gcls : groups)
+          if (gcls[0]->rv == c->rv && gcls[0]->N == c->N && gcls[0]->prec == c->prec && gcls[0]->Rp == c->Rp) {
+            gcls.push_back(c);
+            placed = true;
+            break;
+          }
+        if (!placed) groups.push_back({c});
+      }
+      for (auto& gcls : groups) {
+        PlanClass pc;
+        pc.rv = gcls[0]->rv;
+        pc.nother = gcls[0]->N - 1;
+        pc.Rp = gcls[0]->Rp;
+        pc.prec = gcls[0]->prec;
+        pc.njobs = (int)gcls.size();
+        std::vector<StepDesc> cd;
+        std::vector<int64_t> tl, gb;
+        for (sacd_ctx* c : gcls) {
+          cd.push_back(c->hdesc[n]);
+          tl.push_back(c->m[n].ntiles);
+          gb.push_back(c->m[n].gram_blocks);
+        }
+        pc.tiles = tot(tl);
+        pc.gram_blocks = tot(gb);
+        TRY(alloc_copy(&pc.d_descs, cd, st));
+        TRY(alloc_copy(&pc.d_tile_base, prefix(tl), st));
+        TRY(alloc_copy(&pc.d_gram_base, prefix(gb), st));
+        pm.classes.push_back(pc);
+      }
+    }
+    // batched objective
+    std::vector<FitDesc> fds;
+    std::vector<int64_t> fb;
+    for (int j = 0; j < njobs; ++j) fds.push_back(jobs[j]->hfit), fb.push_back(jobs[j]->fit_blocks);
+    fit_blocks = 0;
+    for (auto x : fb) fit_blocks += x;
+    std::vector<double> zeros((size_t)njobs * 4, 0.0);
+    TRY(alloc_copy(&d_fit_out, zeros, st));
+    for (int j = 0; j < njobs; ++j) fds[j].out = d_fit_out + 4 * j;
+    TRY(alloc_copy(&d_fit, fds, st));
+    TRY(alloc_copy(&d_fit_base, prefix(fb), st));
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(SACD_ECUDA, "batch plan upload failed");
+    return SACD_OK;
+  }
+
+  // One outer iteration of every job (mode steps 0..maxN-1; a job takes part in the modes it has).
+  void enqueue_iteration(cudaStream_t st) const {
+    for (int n = 0; n < maxN; ++n) {
+      const PlanMode& pm = modes[n];
+      if (!pm.njobs) continue;
+      launch_hl(pm.d_descs, pm.njobs, st);
+      for (sacd_ctx* c : pm.empty_jobs)
+        cudaMemsetAsync(c->m[n].M, 0, (size_t)c->m[n].I * c->Rp * sizeof(float), st);
+      for (const PlanClass& pc : pm.classes)
+        launch_mttkrp(pc.d_descs, pc.d_tile_base, pc.njobs, pc.tiles, pc.prec, pc.rv, pc.nother, st);
+      launch_fixup_light(pm.d_descs, pm.d_light, pm.njobs, pm.light, st);
+      launch_fixup_chunks(pm.d_descs, pm.d_chunk, pm.njobs, pm.chunk, st);
+      launch_fixup_heavy(pm.d_descs, pm.d_heavy, pm.njobs, pm.heavy, st);
+      launch_pass1(pm.d_descs, pm.d_p1, pm.njobs, pm.p1, pm.smem, st);
+      launch_pass2(pm.d_descs, pm.d_p2, pm.njobs, pm.p2, pm.smem, st);
+      for (const PlanClass& pc : pm.classes)
+        launch_gram(pc.d_descs, pc.d_gram_base, pc.njobs, pc.gram_blocks, pc.Rp, st);
+      launch_gram_reduce(pm.d_descs, pm.d_gr, pm.njobs, pm.gr, st);
+    }
+  }
+
+  void enqueue_fit(cudaStream_t st) const { launch_fit(d_fit, d_fit_base, njobs, fit_blocks, st); }
+};
+
+}  // namespace
+
+struct sacd_batch {
+  std::vector<sacd_ctx*> jobs;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  bool poisoned = false;
+  BatchPlan plan;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+};
+
+extern "C" {
+
+sacd_status sacd_batch_create(const sacd_config* cfgs, int32_t njobs, void* stream, sacd_batch** out) {
+  if (!out) return fail(SACD_EINVAL, "null out");
+  *out = nullptr;
+  if (!cfgs || njobs < 1) return fail(SACD_EINVAL, "need at least one job configuration");
+  sacd_batch* b = new (std::nothrow) sacd_batch();
+  if (!b) return fail(SACD_ENOMEM, "host allocation failed");
+  try {
+    if (stream) {
+      b->st = reinterpret_cast<cudaStream_t>(stream);
+    } else {
+      if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+        delete b;
+        return fail(SACD_ECUDA, "cudaStreamCreate failed");
+      }
+      b->own_stream = true;
+    }
+    for (int j = 0; j < njobs; ++j) {
+      sacd_config c = cfgs[j];
+      c.stream = b->st;
+      sacd_ctx* ctx = nullptr;
+      const sacd_status s = sacd_create(&c, &ctx);
+      if (s != SACD_OK) {
+        const std::string msg = "job " + std::to_string(j) + ": " + g_err;
+        sacd_batch_destroy(b);
+        return fail(s, msg);
+      }
+      b->jobs.push_back(ctx);
+    }
+    const sacd_status s = b->plan.build(b->jobs, b->st);
+    if (s != SACD_OK) {
+      sacd_batch_destroy(b);
+      return s;
+    }
+  } catch (const std::bad_alloc&) {
+    sacd_batch_destroy(b);
+    return fail(SACD_ENOMEM, "host allocation failed");
+  }
+  *out = b;
+  return SACD_OK;
+}
+
+sacd_status sacd_batch_iterate(sacd_batch* b, int32_t iters) {
+  if (!b) return fail(SACD_EINVAL, "null batch");
+  if (b->poisoned) return fail(SACD_ESTATE, "batch is poisoned by an earlier CUDA error");
+  if (iters < 0) return fail(SACD_EINVAL, "iters < 0");
+  if (iters == 0) return SACD_OK;
+  for (sacd_ctx* c : b->jobs)
+    if (c->replay_mode >= 0) return fail(SACD_ESTATE, "a job has a pending replay mask");
+  cudaError_t e;
+  if (!b->gexec) {
+    e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      b->plan.enqueue_iteration(b->st);
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(b->st, &g);
+      b->graph = g;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, b->graph, 0);
+    }
+    if (e != cudaSuccess) {
+      b->poisoned = true;
+      return fail(SACD_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+    }
+  }
+  for (int it = 0; it < iters; ++it) {
+    e = cudaGraphLaunch(b->gexec, b->st);
+    if (e != cudaSuccess) {
+      b->poisoned = true;
+      return fail(SACD_ECUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
+    }
+  }
+  for (sacd_ctx* c : b->jobs) {
+    c->last_mode = c->N - 1;
+    c->mlast_valid = true;
+  }
+  return SACD_OK;
+}
+
+sacd_status sacd_batch_fit(sacd_batch* b, double* objective, double* fit) {
+  if (!b) return fail(SACD_EINVAL, "null batch");
+  if (b->poisoned) return fail(SACD_ESTATE, "batch is poisoned by an earlier CUDA error");
+  for (sacd_ctx* c : b->jobs)
+    if (!c->mlast_valid) {
+      enqueue_mttkrp(c, c->N - 1);
+      c->mlast_valid = true;
+    }
+  b->plan.enqueue_fit(b->st);
+  std::vector<double> out((size_t)b->jobs.size() * 4);
+  cudaError_t e = cudaMemcpyAsync(out.data(), b->plan.d_fit_out, sizeof(double) * out.size(), cudaMemcpyDeviceToHost,
+                                  b->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) {
+    b->poisoned = true;
+    return fail(SACD_ECUDA, std::string("batch fit: ") + cudaGetErrorString(e));
+  }
+  for (size_t j = 0; j < b->jobs.size(); ++j) {
+    if (objective) objective[j] = out[4 * j];
+    if (fit) fit[j] = out[4 * j + 1];
+  }
+  return SACD_OK;
+}
+
+sacd_status sacd_batch_job(sacd_batch* b, int32_t job, sacd_ctx** ctx_out) {
+  if (!b || !ctx_out || job < 0 || job >= (int)b->jobs.size()) return fail(SACD_EINVAL, "bad batch or job");
+  *ctx_out = b->jobs[job];
+  return SACD_OK;
+}
+
+void sacd_batch_destroy(sacd_batch* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->plan.release();
+  for (sacd_ctx* c : b->jobs) sacd_destroy(c);
+  if (b->own_stream && b->st) cudaStreamDestroy(b->st);
+  cudaGetLastError();
+  delete b;
+}
 
 }  // extern "C"

@@ -104,7 +104,7 @@ void launch_hl(const StepDesc* d_descs, int njobs, cudaStream_t st) {
 int rows_per_block(int Rp) { return 256 / (Rp / 8); }
 int rows_per_block_pass1(int Rp) { return rows_per_block(Rp); }
 int rows_per_block_pass2(int Rp) { return rows_per_block(Rp); }
-static size_t pass_smem_bytes(int Rp) {
+size_t pass_smem_bytes(int Rp) {
   const int RB = rows_per_block(Rp);
   size_t b = (size_t)RB * (Rp + 1) * sizeof(float);  // staged A rows
   if (Rp <= 64) b += (size_t)Rp * Rp * sizeof(float);  // H
@@ -228,10 +228,10 @@ __global__ void __launch_bounds__(256) pass1_kernel(const StepDesc* __restrict__
   }
 }
 
-void launch_pass1(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+void launch_pass1(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, size_t smem,
                   cudaStream_t st) {
   if (total_blocks <= 0) return;
-  pass1_kernel<<<(unsigned)total_blocks, 256, pass_smem_bytes(Rp), st>>>(d_descs, d_base, njobs);
+  pass1_kernel<<<(unsigned)total_blocks, 256, smem, st>>>(d_descs, d_base, njobs);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -339,37 +339,43 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
     }
     __syncwarp();
     bool upd = false;
-    for (int r = 0; r < R; ++r) {
-      if (!((selb[r2 * TPR + (r >> 3)] >> (r & 7)) & 1u)) continue;
-      const float ar = arow[r];
-      float g;
-      if (gs && upd) {
-        float hi = 0.f, lo = 0.f;
-        for (int k = 0; k < CPL; ++k) {
-          const int j = lane + 32 * k;
-          if (j < R) dot2_acc(arow[j], Hr[r * Rp + j], hi, lo);  // H is symmetric: H[j][r] = H[r][j]
-        }
+    const uint8_t* rsel = selb + r2 * TPR;
+    for (int w0 = 0; w0 < TPR; w0 += 4) {  // 32 columns per word, selected columns in order
+      uint32_t bits = 0;
+      for (int k = 0; k < 4 && w0 + k < TPR; ++k) bits |= (uint32_t)rsel[w0 + k] << (8 * k);
+      while (bits) {
+        const int r = w0 * 8 + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const float ar = arow[r];
+        float g;
+        if (gs && upd) {
+          float hi = 0.f, lo = 0.f;
+          for (int k = 0; k < CPL; ++k) {
+            const int j = lane + 32 * k;
+            if (j < R) dot2_acc(arow[j], Hr[r * Rp + j], hi, lo);  // H is symmetric: H[j][r] = H[r][j]
+          }
 #pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-          const float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
-          const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
-          float s, t;
-          two_sum(hi, ohi, s, t);
-          hi = s;
-          lo = __fadd_rn(__fadd_rn(lo, olo), t);
+          for (int off = 16; off >= 1; off >>= 1) {
+            const float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
+            const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
+            float s2, t2;
+            two_sum(hi, ohi, s2, t2);
+            hi = s2;
+            lo = __fadd_rn(__fadd_rn(lo, olo), t2);
+          }
+          float s2, t2;
+          two_sum(hi, -mrow[r], s2, t2);
+          g = __fadd_rn(s2, __fadd_rn(lo, t2));
+        } else {
+          g = grow[r];
         }
-        float s, t;
-        two_sum(hi, -mrow[r], s, t);
-        g = __fadd_rn(s, __fadd_rn(lo, t));
-      } else {
-        g = grow[r];
-      }
-      const float s = sacd_step(ar, g, __ldg(invh + r));
-      if (s != 0.f) {
-        __syncwarp();
-        if (lane == 0) arow[r] = __fadd_rn(ar, s);
-        __syncwarp();
-        upd = true;
+        const float s = sacd_step(ar, g, __ldg(invh + r));
+        if (s != 0.f) {
+          __syncwarp();
+          if (lane == 0) arow[r] = __fadd_rn(ar, s);
+          __syncwarp();
+          upd = true;
+        }
       }
     }
     if (upd) {
@@ -383,10 +389,10 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
   }
 }
 
-void launch_pass2(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+void launch_pass2(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, size_t smem,
                   cudaStream_t st) {
   if (total_blocks <= 0) return;
-  pass2_kernel<<<(unsigned)total_blocks, 256, pass_smem_bytes(Rp), st>>>(d_descs, d_base, njobs);
+  pass2_kernel<<<(unsigned)total_blocks, 256, smem, st>>>(d_descs, d_base, njobs);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -512,11 +518,15 @@ void launch_gram_reduce(const StepDesc* d_descs, const int64_t* d_base, int njob
 
 // ------------------------------------------------------------------------------------------
 // objective and fit
-__global__ void __launch_bounds__(256) fit_kernel(const FitDesc* __restrict__ fdp) {
-  const FitDesc& f = *fdp;
+__global__ void __launch_bounds__(256) fit_kernel(const FitDesc* __restrict__ fds, const int64_t* __restrict__ base,
+                                                 int njobs) {
+  const int jb = njobs > 1 ? find_job(base, njobs, (int64_t)blockIdx.x) : 0;
+  const FitDesc& f = fds[jb];
+  const int64_t lb = (int64_t)blockIdx.x - base[jb];
+  const int64_t nblk = base[jb + 1] - base[jb];
   __shared__ double red[256];
   __shared__ int amlast;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = lb * blockDim.x + threadIdx.x;
   double part = 0.0;
   if (i < f.I) {
     float hi = 0.f, lo = 0.f;
@@ -533,16 +543,16 @@ __global__ void __launch_bounds__(256) fit_kernel(const FitDesc* __restrict__ fd
   }
   const double bs = block_sum(part, red);
   if (threadIdx.x == 0) {
-    f.part[blockIdx.x] = bs;
+    f.part[lb] = bs;
     __threadfence();
     const unsigned prev = atomicAdd(f.counter, 1u);
-    amlast = (prev == gridDim.x - 1u);
+    amlast = (prev == (unsigned)nblk - 1u);
   }
   __syncthreads();
   if (amlast) {
     __threadfence();
     double s = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(f.part + b);
+    for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(f.part + b);
     const double inner = block_sum(s, red);
     double mn = 0.0;
     for (int e = threadIdx.x; e < f.R * f.R; e += blockDim.x) {
@@ -563,8 +573,9 @@ __global__ void __launch_bounds__(256) fit_kernel(const FitDesc* __restrict__ fd
   }
 }
 
-void launch_fit(const FitDesc* d_fit, int64_t blocks, cudaStream_t st) {
-  fit_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(d_fit);
+// base[0..njobs]: prefix of the jobs' block counts (ceil(I / 256) of their last mode)
+void launch_fit(const FitDesc* d_fit, const int64_t* d_base, int njobs, int64_t total_blocks, cudaStream_t st) {
+  fit_kernel<<<(unsigned)(total_blocks > 0 ? total_blocks : 1), 256, 0, st>>>(d_fit, d_base, njobs);
 }
 
 // ------------------------------------------------------------------------------------------

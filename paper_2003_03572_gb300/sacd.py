@@ -42,6 +42,12 @@ __all__ = [
     "sacd_mttkrp_noalloc",
     "sacd_destroy",
     "sacd_last_error",
+    "sacd_batch_create",
+    "sacd_batch_iterate",
+    "sacd_batch_fit",
+    "sacd_batch_job",
+    "sacd_batch_destroy",
+    "SaCDBatch",
     "SaCD",
 ]
 
@@ -128,6 +134,11 @@ def lib():
         "sacd_profile_enable": (C.c_int, [vp, i32]),
         "sacd_profile_read": (C.c_int, [vp, C.POINTER(sacd_kernel_stat), i32, C.POINTER(i32)]),
         "sacd_mttkrp_noalloc": (C.c_int, [i32, i32, C.POINTER(i64), i64, vp, vp, vp, C.POINTER(vp), i32, i32, vp, vp]),
+        "sacd_batch_create": (C.c_int, [C.POINTER(sacd_config), i32, vp, C.POINTER(vp)]),
+        "sacd_batch_iterate": (C.c_int, [vp, i32]),
+        "sacd_batch_fit": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(dbl)]),
+        "sacd_batch_job": (C.c_int, [vp, i32, C.POINTER(vp)]),
+        "sacd_batch_destroy": (None, [vp]),
         "sacd_destroy": (None, [vp]),
         "sacd_last_error": (C.c_char_p, []),
     }
@@ -155,11 +166,9 @@ def _ptr(a):
     return a.ctypes.data
 
 
-def sacd_create(dims, idx, vals, rank, init=None, *, seed=0, precision=SACD_FP32, lnorm=SACD_LNORM_FRO,
-                fixup=SACD_FIXUP_COLUMN_GS, stream=None, on_device=False):
-    """Create a context. ``idx``: sequence of N int32 arrays (or an (N, nnz) array), ``vals``:
-    float32 (nnz,), ``init``: N float32 (I_n, R) arrays or None. With ``on_device`` the arrays are
-    CUDA tensors. Returns the opaque context handle (an int)."""
+def _make_config(dims, idx, vals, rank, init=None, *, seed=0, precision=SACD_FP32, lnorm=SACD_LNORM_FRO,
+                 fixup=SACD_FIXUP_COLUMN_GS, stream=None, on_device=False):
+    """A sacd_config plus the Python objects that must stay alive while it is used."""
     N = len(dims)
     keep = []
     if on_device:
@@ -190,10 +199,58 @@ def sacd_create(dims, idx, vals, rank, init=None, *, seed=0, precision=SACD_FP32
     cfg.fixup = int(fixup)
     cfg.inputs_on_device = 1 if on_device else 0
     cfg.stream = stream
+    keep += [dims_a, idx_p, init_p]
+    return cfg, keep
+
+
+def sacd_create(dims, idx, vals, rank, init=None, **kw):
+    """Create a context. ``idx``: sequence of N int32 arrays (or an (N, nnz) array), ``vals``:
+    float32 (nnz,), ``init``: N float32 (I_n, R) arrays or None. With ``on_device=True`` the arrays
+    are CUDA tensors. Returns the opaque context handle (an int)."""
+    cfg, keep = _make_config(dims, idx, vals, rank, init, **kw)
     out = C.c_void_p()
     _check(lib().sacd_create(C.byref(cfg), C.byref(out)))
     del keep
     return out.value
+
+
+def sacd_batch_create(jobs, stream=None):
+    """Create a batch from a list of dicts with the keyword arguments of ``sacd_create``
+    (dims, idx, vals, rank, init, precision, ...). Returns the opaque batch handle."""
+    cfgs = (sacd_config * len(jobs))()
+    keep = []
+    for j, spec in enumerate(jobs):
+        spec = dict(spec)
+        cfg, k = _make_config(spec.pop("dims"), spec.pop("idx"), spec.pop("vals"), spec.pop("rank"),
+                              spec.pop("init", None), **spec)
+        cfgs[j] = cfg
+        keep.append(k)
+    out = C.c_void_p()
+    _check(lib().sacd_batch_create(cfgs, len(jobs), stream, C.byref(out)))
+    del keep
+    return out.value
+
+
+def sacd_batch_iterate(b, iters):
+    _check(lib().sacd_batch_iterate(b, int(iters)))
+
+
+def sacd_batch_fit(b, njobs):
+    o = (C.c_double * njobs)()
+    f = (C.c_double * njobs)()
+    _check(lib().sacd_batch_fit(b, o, f))
+    return np.array(o[:]), np.array(f[:])
+
+
+def sacd_batch_job(b, job):
+    out = C.c_void_p()
+    _check(lib().sacd_batch_job(b, int(job), C.byref(out)))
+    return out.value
+
+
+def sacd_batch_destroy(b):
+    if b:
+        lib().sacd_batch_destroy(b)
 
 
 def sacd_mode_step(ctx, mode, want_count=True):
@@ -358,6 +415,44 @@ class SaCD:
         if self.ctx:
             sacd_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SaCDBatch:
+    """Owning wrapper around a batch of independent jobs (see sacd_batch_* in include/sacd.h)."""
+
+    def __init__(self, jobs, stream=None):
+        self.njobs = len(jobs)
+        self.b = sacd_batch_create(jobs, stream)
+
+    def iterate(self, iters):
+        sacd_batch_iterate(self.b, iters)
+
+    def fit(self):
+        return sacd_batch_fit(self.b, self.njobs)
+
+    def job(self, j):
+        """The j-th job's context handle (borrowed: the batch keeps owning it)."""
+        return sacd_batch_job(self.b, j)
+
+    def factor(self, j, mode):
+        return sacd_get_factor(self.job(j), mode)
+
+    def close(self):
+        if self.b:
+            sacd_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self
