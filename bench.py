@@ -438,6 +438,75 @@ def batched_arm(args):
     return 0
 
 
+def serve_arm(args):
+    """Served workload: Poisson arrivals of 3- and 4-mode BF16-gather jobs, continuous batching
+    with HBM-budget admission; solves/s and arrival-to-result latency percentiles."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import numpy as np
+    import torch
+
+    from paper_2003_03572_gb300 import sacd as S
+    from paper_2003_03572_gb300 import serve, synth
+
+    tensors, jobs = synth.serving_workloads(args.jobs, pool=args.pool)
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4), mp_context=mp.get_context("spawn")) as ex:
+        data = list(ex.map(_gen_job_tensor, tensors, chunksize=1))
+    torch.cuda.init()
+    stream = torch.cuda.Stream()
+    specs = []
+    for ti, R, seed in jobs:
+        w = tensors[ti]
+        specs.append(dict(dims=w.dims, idx=data[ti][0], vals=data[ti][1], rank=R, init=None, seed=seed,
+                          precision=S.SACD_BF16_GATHER))
+    iters = tensors[0].iters
+    arrivals = serve.poisson_arrivals(args.rate, len(specs), 0x5ACD0004)
+    sample = set(range(0, len(specs), max(1, len(specs) // 4)))
+    with serve.Server(int(args.budget_gb * 2**30), stream=stream.cuda_stream) as srv:
+        # warm-up: one small job (module loading, allocator) before the clock starts
+        sm = min(range(len(specs)), key=lambda i: tensors[jobs[i][0]].nnz)
+        serve.run_arrivals(srv, [specs[sm]], [0.0], 2)
+        res, wall = serve.run_arrivals(srv, specs, arrivals, iters, keep_for=sample)
+        st = srv.stats()
+    ok = [r for r in res if r["status"] == 0]
+    # each sampled job again, alone, from its own context: same factors as in the mix
+    same = True
+    for r in res:
+        if r["index"] in sample and "factors" in r:
+            sp = specs[r["index"]]
+            with S.SaCD(sp["dims"], sp["idx"], sp["vals"], sp["rank"], None, seed=sp["seed"],
+                        precision=sp["precision"], stream=stream.cuda_stream) as a:
+                a.iterate(iters)
+                same &= all(np.array_equal(a.factor(n), r["factors"][n]) for n in range(len(sp["dims"])))
+    summ = serve.latency_summary(res)
+    line = {
+        "metric": "served SaCD solves/s",
+        "value": len(ok) / wall,
+        "unit": "solves/s",
+        "latency": summ,
+        "jobs": len(specs),
+        "completed": len(ok),
+        "failed": len(res) - len(ok),
+        "wall_s": wall,
+        "same_alone_and_in_mix": bool(same),
+        "peak_device_bytes": st["peak_bytes"],
+        "server_steps": st["steps"],
+        "config": {"workload": f"Poisson arrivals {args.rate}/s, {len(specs)} jobs, N in {{3,4}}, dims log-uniform "
+                               f"[500,100000], nnz log-uniform [50k,5M], Zipf(1.1), R in {{16,32,64}}, BF16 gathers, "
+                               f"{iters} iterations, {args.budget_gb} GiB budget, {len(tensors)} distinct tensors",
+                   "nnz_per_job_mean": float(np.mean([tensors[t].nnz for t, _, _ in jobs]))},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _gen_job_tensor(w):
+    from paper_2003_03572_gb300 import synth
+
+    return synth.sparse_tensor(w.dims, w.nnz, dist=w.dist, zipf_s=w.zipf_s, values=w.values, seed=w.seed)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,6 +520,10 @@ def main():
     ap.add_argument("--cpu-baseline-child", action="store_true")
     ap.add_argument("--batched", action="store_true", help="the many-small-jobs workload (batched vs one at a time)")
     ap.add_argument("--jobs", type=int, default=512)
+    ap.add_argument("--serve", action="store_true", help="the served workload (Poisson arrivals, continuous batching)")
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--pool", type=int, default=64)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
     args = ap.parse_args()
     if args.cpu_baseline_child:
         cpu_baseline_child(args.workload, args.steps)
@@ -461,6 +534,8 @@ def main():
         return reference_arm(args)
     if args.batched:
         return batched_arm(args)
+    if args.serve:
+        return serve_arm(args)
     return ours_arm(args)
 
 

@@ -247,6 +247,50 @@ sacd_status sacd_batch_fit(sacd_batch* b, double* objective, double* fit);
 sacd_status sacd_batch_job(sacd_batch* b, int32_t job, sacd_ctx** ctx_out);
 void sacd_batch_destroy(sacd_batch* b);
 
+/*
+ * Serving (not in the paper; the served workload): continuous batching of factorisation jobs
+ * on one GPU, single-threaded API.
+ *  - sacd_server_create: `hbm_budget_bytes` caps the device memory of admitted jobs (each job is
+ *    charged an upper bound of its create-time peak until it is admitted, then the bytes its
+ *    context holds); at most `max_active` jobs run at once; `stream` as for contexts.
+ *  - sacd_server_submit: queue a job (FIFO) that will run `iters` outer iterations. The arrays
+ *    that cfg points to are read when the job is admitted and must stay valid until its result
+ *    has been drained by sacd_server_results. cfg->stream is ignored.
+ *  - sacd_server_step: admit waiting jobs in order while they fit the budget (a job larger than
+ *    the whole budget finishes with SACD_ENOMEM; a job whose create fails finishes with that
+ *    status), run one outer iteration of every admitted job with one batched launch set, and
+ *    finish the jobs that reached their iteration count: objective and fit evaluated, factors
+ *    copied to host memory, device memory freed. Waits for the GPU. Reports active and waiting
+ *    counts (nullable).
+ *  - sacd_server_results: drain up to `cap` finished jobs' results (times are seconds since the
+ *    server was created, host clock); their factors stay available through
+ *    sacd_server_get_factor (I_n x R FP32) until sacd_server_release.
+ * A job's results are the same as those of its own context run alone.
+ */
+typedef struct sacd_server sacd_server;
+typedef struct {
+  int64_t job_id;
+  int32_t status;      /* sacd_status of the job */
+  int32_t iters;       /* iterations run */
+  double objective;
+  double fit;
+  double t_submit, t_admit, t_done;
+  int64_t device_bytes;
+  char error[128];
+} sacd_job_result;
+typedef struct {
+  int32_t active, waiting, finished;
+  int64_t used_bytes, peak_bytes, budget_bytes, steps;
+} sacd_server_stats_t;
+sacd_status sacd_server_create(int64_t hbm_budget_bytes, int32_t max_active, void* stream, sacd_server** out);
+sacd_status sacd_server_submit(sacd_server* s, const sacd_config* cfg, int32_t iters, int64_t* job_id);
+sacd_status sacd_server_step(sacd_server* s, int32_t* n_active, int32_t* n_waiting);
+sacd_status sacd_server_results(sacd_server* s, sacd_job_result* out, int32_t cap, int32_t* n);
+sacd_status sacd_server_get_factor(sacd_server* s, int64_t job_id, int32_t mode, float* host_out);
+sacd_status sacd_server_release(sacd_server* s, int64_t job_id);
+sacd_status sacd_server_stats(sacd_server* s, sacd_server_stats_t* out);
+void sacd_server_destroy(sacd_server* s);
+
 /* sacd_destroy -- release everything the context owns. NULL-safe; legal on a poisoned context. */
 void sacd_destroy(sacd_ctx* ctx);
 

@@ -1377,3 +1377,308 @@ void sacd_batch_destroy(sacd_batch* b) {
 }
 
 }  // extern "C"
+
+// ==========================================================================================
+// Serving: continuous batching of factorisation jobs. Jobs wait in FIFO order until the device
+// memory they need fits the budget; every step runs one outer iteration of every admitted job
+// with one batched launch set; a job that reached its iteration count is finished (objective,
+// fit and factors copied to the host) and its device memory is freed at once, so waiting jobs
+// join at the next step. Per-job arithmetic is the context's own: results do not depend on the
+// mix.
+#include <chrono>
+#include <deque>
+#include <map>
+
+namespace {
+
+struct ServerJob {
+  int64_t id = 0;
+  sacd_config cfg{};
+  std::vector<int64_t> dims;
+  std::vector<const int32_t*> idx;
+  std::vector<const float*> init;
+  int32_t iters = 0, done_iters = 0;
+  int64_t est_bytes = 0, bytes = 0;
+  double t_submit = 0, t_admit = -1, t_done = -1;
+  sacd_ctx* ctx = nullptr;
+  int32_t status = 0;
+  std::string error;
+  double objective = 0, fit = 0;
+  std::vector<std::vector<float>> factors;
+};
+
+// Upper bound of the device bytes a context of this configuration holds at its peak (during
+// sacd_create, when the sort buffers and the unsorted copy coexist with the slice structures).
+int64_t estimate_bytes(const sacd_config* c) {
+  const int64_t N = c->nmodes, nnz = c->nnz;
+  int Rp = 8;
+  while (Rp < c->rank) Rp <<= 1;
+  int64_t rows = 0, Imax = 0;
+  for (int n = 0; n < N; ++n) {
+    rows += c->dims[n];
+    Imax = std::max<int64_t>(Imax, c->dims[n]);
+  }
+  const int64_t csf = N * nnz * 4 * (N + 1);
+  const int64_t facs = rows * Rp * (12 + (c->precision == SACD_BF16_GATHER ? 2 : 0)) + N * (int64_t)Rp * Rp * 8;
+  const int64_t tiles = nnz / 32 + 1;
+  const int64_t gram_blocks = std::min<int64_t>((Imax + 4096 / Rp - 1) / (4096 / Rp), 4 * 152);
+  const int64_t scratch = Imax * Rp * 6 + tiles * (2 * Rp * 4 + 16) + gram_blocks * Rp * Rp * 8 + (1 << 20);
+  const int64_t temps = nnz * (12 * N + 64) + (nnz / 2048 + 1) * 256 * 12;
+  return (csf + facs + scratch + temps) * 11 / 10;
+}
+
+double now_s(const std::chrono::steady_clock::time_point& t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+struct sacd_server {
+  int64_t budget = 0;
+  int32_t max_active = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  bool poisoned = false;
+  int64_t used = 0, peak_used = 0;
+  int64_t next_id = 1;
+  std::chrono::steady_clock::time_point t0;
+  std::deque<ServerJob*> waiting;
+  std::vector<ServerJob*> active;
+  std::deque<ServerJob*> finished;    // results not drained yet
+  std::map<int64_t, ServerJob*> kept; // drained, factors kept until released
+  BatchPlan plan;
+  bool plan_dirty = true;
+  int64_t steps = 0;
+};
+
+namespace {
+
+void finish_job(sacd_server* s, ServerJob* j) {
+  j->t_done = now_s(s->t0);
+  if (j->ctx) {
+    s->used -= j->bytes;
+    sacd_destroy(j->ctx);
+    j->ctx = nullptr;
+  }
+  s->finished.push_back(j);
+}
+
+}  // namespace
+
+extern "C" {
+
+sacd_status sacd_server_create(int64_t hbm_budget_bytes, int32_t max_active, void* stream, sacd_server** out) {
+  if (!out) return fail(SACD_EINVAL, "null out");
+  *out = nullptr;
+  if (hbm_budget_bytes <= 0 || max_active < 1) return fail(SACD_EINVAL, "budget and max_active must be positive");
+  sacd_server* s = new (std::nothrow) sacd_server();
+  if (!s) return fail(SACD_ENOMEM, "host allocation failed");
+  s->budget = hbm_budget_bytes;
+  s->max_active = max_active;
+  s->t0 = std::chrono::steady_clock::now();
+  if (stream) {
+    s->st = reinterpret_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete s;
+      return fail(SACD_ECUDA, "cudaStreamCreate failed");
+    }
+    s->own_stream = true;
+  }
+  *out = s;
+  return SACD_OK;
+}
+
+sacd_status sacd_server_submit(sacd_server* s, const sacd_config* cfg, int32_t iters, int64_t* job_id) {
+  if (!s || !cfg || !job_id) return fail(SACD_EINVAL, "null argument");
+  if (s->poisoned) return fail(SACD_ESTATE, "server is poisoned by an earlier CUDA error");
+  if (iters < 1) return fail(SACD_EINVAL, "iters must be >= 1");
+  if (cfg->nmodes < 2 || cfg->nmodes > SACD_MAXN || !cfg->dims) return fail(SACD_EINVAL, "bad nmodes or dims");
+  try {
+    ServerJob* j = new ServerJob();
+    j->id = s->next_id++;
+    j->cfg = *cfg;
+    j->dims.assign(cfg->dims, cfg->dims + cfg->nmodes);
+    j->cfg.dims = j->dims.data();
+    if (cfg->idx) {
+      j->idx.assign(cfg->idx, cfg->idx + cfg->nmodes);
+      j->cfg.idx = j->idx.data();
+    }
+    if (cfg->init) {
+      j->init.assign(cfg->init, cfg->init + cfg->nmodes);
+      j->cfg.init = j->init.data();
+    }
+    j->cfg.stream = s->st;
+    j->iters = iters;
+    j->est_bytes = estimate_bytes(&j->cfg);
+    j->t_submit = now_s(s->t0);
+    s->waiting.push_back(j);
+    *job_id = j->id;
+  } catch (const std::bad_alloc&) {
+    return fail(SACD_ENOMEM, "host allocation failed");
+  }
+  return SACD_OK;
+}
+
+sacd_status sacd_server_step(sacd_server* s, int32_t* n_active, int32_t* n_waiting) {
+  if (!s) return fail(SACD_EINVAL, "null server");
+  if (s->poisoned) return fail(SACD_ESTATE, "server is poisoned by an earlier CUDA error");
+  // ---- admission, FIFO, within the budget
+  while (!s->waiting.empty() && (int)s->active.size() < s->max_active) {
+    ServerJob* j = s->waiting.front();
+    if (!s->active.empty() && s->used + j->est_bytes > s->budget) break;
+    if (j->est_bytes > s->budget) {  // can never fit
+      s->waiting.pop_front();
+      j->status = SACD_ENOMEM;
+      j->error = "job needs more device memory than the whole budget";
+      finish_job(s, j);
+      continue;
+    }
+    s->waiting.pop_front();
+    j->t_admit = now_s(s->t0);
+    sacd_ctx* c = nullptr;
+    const sacd_status st = sacd_create(&j->cfg, &c);
+    if (st != SACD_OK) {
+      j->status = st;
+      j->error = g_err;
+      finish_job(s, j);
+      if (st == SACD_ECUDA) {
+        s->poisoned = true;
+        return fail(SACD_ECUDA, "job " + std::to_string(j->id) + ": " + j->error);
+      }
+      continue;
+    }
+    j->ctx = c;
+    j->bytes = c->device_bytes;
+    s->used += j->bytes;
+    s->peak_used = std::max(s->peak_used, s->used + j->est_bytes - j->bytes);
+    s->active.push_back(j);
+    s->plan_dirty = true;
+  }
+  // ---- one outer iteration of every admitted job
+  if (!s->active.empty()) {
+    if (s->plan_dirty) {
+      s->plan.release();
+      std::vector<sacd_ctx*> ctxs;
+      for (ServerJob* j : s->active) ctxs.push_back(j->ctx);
+      const sacd_status st = s->plan.build(ctxs, s->st);
+      if (st != SACD_OK) {
+        s->poisoned = true;
+        return st;
+      }
+      s->plan_dirty = false;
+    }
+    s->plan.enqueue_iteration(s->st);
+    s->steps++;
+    std::vector<ServerJob*> still;
+    for (ServerJob* j : s->active) {
+      j->done_iters++;
+      j->ctx->last_mode = j->ctx->N - 1;
+      j->ctx->mlast_valid = true;
+      if (j->done_iters < j->iters) {
+        still.push_back(j);
+        continue;
+      }
+      sacd_status st = sacd_fit(j->ctx, &j->objective, &j->fit);
+      if (st == SACD_OK) {
+        j->factors.resize(j->ctx->N);
+        for (int n = 0; n < j->ctx->N && st == SACD_OK; ++n) {
+          j->factors[n].resize((size_t)j->ctx->m[n].I * j->ctx->R);
+          st = sacd_get_factor(j->ctx, n, j->factors[n].data());
+        }
+      }
+      if (st != SACD_OK) {
+        s->poisoned = true;
+        j->status = st;
+        j->error = g_err;
+        finish_job(s, j);
+        return fail(st, "job " + std::to_string(j->id) + ": " + j->error);
+      }
+      finish_job(s, j);
+      s->plan_dirty = true;
+    }
+    s->active.swap(still);
+    const cudaError_t e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) {
+      s->poisoned = true;
+      return fail(SACD_ECUDA, std::string("server step: ") + cudaGetErrorString(e));
+    }
+  }
+  if (n_active) *n_active = (int32_t)s->active.size();
+  if (n_waiting) *n_waiting = (int32_t)s->waiting.size();
+  return SACD_OK;
+}
+
+sacd_status sacd_server_results(sacd_server* s, sacd_job_result* out, int32_t cap, int32_t* n) {
+  if (!s || !n) return fail(SACD_EINVAL, "null argument");
+  int32_t k = 0;
+  while (!s->finished.empty() && k < cap) {
+    ServerJob* j = s->finished.front();
+    s->finished.pop_front();
+    sacd_job_result& r = out[k++];
+    memset(&r, 0, sizeof(r));
+    r.job_id = j->id;
+    r.status = j->status;
+    r.iters = j->done_iters;
+    r.objective = j->objective;
+    r.fit = j->fit;
+    r.t_submit = j->t_submit;
+    r.t_admit = j->t_admit;
+    r.t_done = j->t_done;
+    r.device_bytes = j->bytes;
+    strncpy(r.error, j->error.c_str(), sizeof(r.error) - 1);
+    s->kept[j->id] = j;
+  }
+  *n = k;
+  return SACD_OK;
+}
+
+sacd_status sacd_server_get_factor(sacd_server* s, int64_t job_id, int32_t mode, float* host_out) {
+  if (!s || !host_out) return fail(SACD_EINVAL, "null argument");
+  auto it = s->kept.find(job_id);
+  if (it == s->kept.end()) return fail(SACD_EINVAL, "unknown job (not finished, not drained, or released)");
+  ServerJob* j = it->second;
+  if (j->status != SACD_OK) return fail(SACD_ESTATE, "job failed: " + j->error);
+  if (mode < 0 || mode >= (int)j->factors.size()) return fail(SACD_EINVAL, "mode out of range");
+  memcpy(host_out, j->factors[mode].data(), j->factors[mode].size() * sizeof(float));
+  return SACD_OK;
+}
+
+sacd_status sacd_server_release(sacd_server* s, int64_t job_id) {
+  if (!s) return fail(SACD_EINVAL, "null server");
+  auto it = s->kept.find(job_id);
+  if (it == s->kept.end()) return fail(SACD_EINVAL, "unknown job");
+  delete it->second;
+  s->kept.erase(it);
+  return SACD_OK;
+}
+
+sacd_status sacd_server_stats(sacd_server* s, sacd_server_stats_t* out) {
+  if (!s || !out) return fail(SACD_EINVAL, "null argument");
+  out->active = (int32_t)s->active.size();
+  out->waiting = (int32_t)s->waiting.size();
+  out->finished = (int32_t)s->finished.size();
+  out->used_bytes = s->used;
+  out->peak_bytes = s->peak_used;
+  out->budget_bytes = s->budget;
+  out->steps = s->steps;
+  return SACD_OK;
+}
+
+void sacd_server_destroy(sacd_server* s) {
+  if (!s) return;
+  if (s->st) cudaStreamSynchronize(s->st);
+  s->plan.release();
+  for (ServerJob* j : s->active) {
+    if (j->ctx) sacd_destroy(j->ctx);
+    delete j;
+  }
+  for (ServerJob* j : s->waiting) delete j;
+  for (ServerJob* j : s->finished) delete j;
+  for (auto& kv : s->kept) delete kv.second;
+  if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+  cudaGetLastError();
+  delete s;
+}
+
+}  // extern "C"

@@ -48,6 +48,14 @@ __all__ = [
     "sacd_batch_job",
     "sacd_batch_destroy",
     "SaCDBatch",
+    "sacd_server_create",
+    "sacd_server_submit",
+    "sacd_server_step",
+    "sacd_server_results",
+    "sacd_server_get_factor",
+    "sacd_server_release",
+    "sacd_server_stats",
+    "sacd_server_destroy",
     "SaCD",
 ]
 
@@ -98,6 +106,33 @@ class sacd_info(C.Structure):
     ]
 
 
+class sacd_job_result(C.Structure):
+    _fields_ = [
+        ("job_id", C.c_int64),
+        ("status", C.c_int32),
+        ("iters", C.c_int32),
+        ("objective", C.c_double),
+        ("fit", C.c_double),
+        ("t_submit", C.c_double),
+        ("t_admit", C.c_double),
+        ("t_done", C.c_double),
+        ("device_bytes", C.c_int64),
+        ("error", C.c_char * 128),
+    ]
+
+
+class sacd_server_stats_t(C.Structure):
+    _fields_ = [
+        ("active", C.c_int32),
+        ("waiting", C.c_int32),
+        ("finished", C.c_int32),
+        ("used_bytes", C.c_int64),
+        ("peak_bytes", C.c_int64),
+        ("budget_bytes", C.c_int64),
+        ("steps", C.c_int64),
+    ]
+
+
 class sacd_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -139,6 +174,14 @@ def lib():
         "sacd_batch_fit": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(dbl)]),
         "sacd_batch_job": (C.c_int, [vp, i32, C.POINTER(vp)]),
         "sacd_batch_destroy": (None, [vp]),
+        "sacd_server_create": (C.c_int, [i64, i32, vp, C.POINTER(vp)]),
+        "sacd_server_submit": (C.c_int, [vp, C.POINTER(sacd_config), i32, C.POINTER(i64)]),
+        "sacd_server_step": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32)]),
+        "sacd_server_results": (C.c_int, [vp, C.POINTER(sacd_job_result), i32, C.POINTER(i32)]),
+        "sacd_server_get_factor": (C.c_int, [vp, i64, i32, vp]),
+        "sacd_server_release": (C.c_int, [vp, i64]),
+        "sacd_server_stats": (C.c_int, [vp, C.POINTER(sacd_server_stats_t)]),
+        "sacd_server_destroy": (None, [vp]),
         "sacd_destroy": (None, [vp]),
         "sacd_last_error": (C.c_char_p, []),
     }
@@ -465,3 +508,63 @@ class SaCDBatch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------------------------ serving
+
+
+def sacd_server_create(hbm_budget_bytes, max_active=1024, stream=None):
+    out = C.c_void_p()
+    _check(lib().sacd_server_create(int(hbm_budget_bytes), int(max_active), stream, C.byref(out)))
+    return out.value
+
+
+def sacd_server_submit(s, spec, iters):
+    """Queue a job (dict with the keyword arguments of sacd_create). Returns (job_id, keep): the
+    arrays in ``keep`` must stay alive until the job's result has been drained."""
+    spec = dict(spec)
+    cfg, keep = _make_config(spec.pop("dims"), spec.pop("idx"), spec.pop("vals"), spec.pop("rank"),
+                             spec.pop("init", None), **spec)
+    jid = C.c_int64()
+    _check(lib().sacd_server_submit(s, C.byref(cfg), int(iters), C.byref(jid)))
+    return jid.value, keep
+
+
+def sacd_server_step(s):
+    a, w = C.c_int32(), C.c_int32()
+    _check(lib().sacd_server_step(s, C.byref(a), C.byref(w)))
+    return a.value, w.value
+
+
+def sacd_server_results(s, cap=256):
+    buf = (sacd_job_result * cap)()
+    n = C.c_int32()
+    _check(lib().sacd_server_results(s, buf, cap, C.byref(n)))
+    out = []
+    for i in range(n.value):
+        r = buf[i]
+        out.append(dict(job_id=r.job_id, status=r.status, iters=r.iters, objective=r.objective, fit=r.fit,
+                        t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done, device_bytes=r.device_bytes,
+                        error=r.error.decode()))
+    return out
+
+
+def sacd_server_get_factor(s, job_id, mode, shape):
+    out = np.empty(shape, dtype=np.float32)
+    _check(lib().sacd_server_get_factor(s, int(job_id), int(mode), out.ctypes.data))
+    return out
+
+
+def sacd_server_release(s, job_id):
+    _check(lib().sacd_server_release(s, int(job_id)))
+
+
+def sacd_server_stats(s):
+    st = sacd_server_stats_t()
+    _check(lib().sacd_server_stats(s, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in sacd_server_stats_t._fields_}
+
+
+def sacd_server_destroy(s):
+    if s:
+        lib().sacd_server_destroy(s)

@@ -38,6 +38,7 @@ __all__ = [
     "zipf_indices",
     "make_workload",
     "batched_workloads",
+    "serving_workloads",
 ]
 
 _I32_MAX = 2**31 - 1
@@ -245,3 +246,26 @@ def batched_workloads(njobs=512, seed=0x5ACD0003, nnz_range=(10_000, 500_000), r
             Workload(f"job{j}", dims, nnz, "zipf", 1.1, "int15", rank, iters, "fp32", seed * 1000003 + j)
         )
     return jobs
+
+
+def serving_workloads(njobs, seed=0x5ACD0004, pool=None, iters=30):
+    """Jobs of the served workload: N in {3, 4} (p = 1/2 each), every mode length log-uniform in
+    [500, 100000], nnz log-uniform in [50k, 5M] (at most half the cells), Zipf(1.1) coordinates,
+    R uniform from {16, 32, 64}, BF16 gathers, `iters` iterations.
+
+    With ``pool`` = P, only P distinct tensors are drawn and job i uses tensor i % P (its own rank
+    and initial factors): a stand-in that keeps the shape and size mix while bounding the time
+    spent drawing inputs. Returns (tensor workloads, per-job (tensor index, rank, init seed))."""
+    rng = _rng(seed)
+    P = njobs if pool is None else min(pool, njobs)
+    tensors = []
+    for t in range(P):
+        N = 3 if rng.random() < 0.5 else 4
+        dims = tuple(int(round(math.exp(rng.uniform(math.log(500), math.log(100_000))))) for _ in range(N))
+        nnz = int(round(math.exp(rng.uniform(math.log(50_000), math.log(5_000_000)))))
+        nnz = min(nnz, math.prod(dims) // 2)
+        tensors.append(Workload(f"serve{t}", dims, nnz, "zipf", 1.1, "int15", 0, iters, "bf16", seed * 7919 + t))
+    jobs = []
+    for j in range(njobs):
+        jobs.append((j % P, int(rng.choice([16, 32, 64])), int(seed * 104729 + j)))
+    return tensors, jobs

@@ -1,0 +1,84 @@
+"""Serving core: continuous batching with HBM-budget admission. Each job's result is the same
+alone and in the mix (bit-identical factors), the budget is respected, and failures injected on
+the host (bad input, a job larger than the budget) finish only the failing job."""
+
+import numpy as np
+import pytest
+
+from paper_2003_03572_gb300 import sacd as S
+from paper_2003_03572_gb300 import serve, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def specs(seed=5):
+    shapes = [((300, 200, 50), 16, 0), ((150, 120, 40, 10), 32, 1), ((400, 90, 30), 64, 1), ((200, 220, 60), 8, 0),
+              ((90, 80, 70, 6), 16, 0), ((500, 60, 25), 32, 1)]
+    out = []
+    for j, (dims, R, bf) in enumerate(shapes):
+        idx, vals = synth.sparse_tensor(dims, 4000 + 1500 * j, dist="zipf", zipf_s=1.1, seed=seed + j)
+        out.append(dict(dims=dims, idx=idx, vals=vals, rank=R, init=synth.init_factors(dims, R, seed + j),
+                        precision=S.SACD_BF16_GATHER if bf else S.SACD_FP32))
+    return out
+
+
+def test_served_results_equal_alone():
+    sp = specs()
+    iters = [5, 8, 3, 6, 4, 7]
+    with serve.Server(1 << 34) as srv:
+        ids = [srv.submit(s, it) for s, it in zip(sp, iters)]
+        done = {}
+        while len(done) < len(sp):
+            srv.step()
+            for r in srv.results():
+                assert r["status"] == 0, r
+                done[r["job_id"]] = (r, srv.factors(r["job_id"]))
+                srv.release(r["job_id"])
+    for jid, s, it in zip(ids, sp, iters):
+        r, F = done[jid]
+        assert r["iters"] == it
+        with S.SaCD(s["dims"], s["idx"], s["vals"], s["rank"], s["init"], precision=s["precision"]) as a:
+            a.iterate(it)
+            for n in range(len(s["dims"])):
+                np.testing.assert_array_equal(F[n], a.factor(n))
+            assert (r["objective"], r["fit"]) == a.fit()
+
+
+def test_budget_admission_and_host_failures():
+    sp = specs(9)
+    bad = dict(sp[0])
+    bad["idx"] = sp[0]["idx"].copy()
+    bad["idx"][0, 0] = 10_000  # out of range: fails at admission, on the host side of the create
+    huge = dict(dims=(100, 100, 100), idx=np.zeros((3, 1), np.int32), vals=np.ones(1, np.float32), rank=8)
+    budget = 40 << 20  # a few small jobs at a time
+    with serve.Server(budget) as srv:
+        jobs = [srv.submit(s, 4) for s in sp[:4]] + [srv.submit(bad, 4)] + [srv.submit(s, 4) for s in sp[4:]]
+        huge_spec = dict(dims=(2_000_000, 2_000_000, 2_000_000), idx=np.zeros((3, 1), np.int32),
+                         vals=np.ones(1, np.float32), rank=256)
+        jh = srv.submit(huge_spec, 2)
+        status = {}
+        max_active = 0
+        while len(status) < len(jobs) + 1:
+            a, w = srv.step()
+            max_active = max(max_active, a)
+            st = srv.stats()
+            assert st["used_bytes"] <= budget
+            for r in srv.results():
+                status[r["job_id"]] = (r["status"], r["error"])
+                srv.release(r["job_id"])
+        assert status[jobs[4]][0] == 1 and "outside" in status[jobs[4]][1]
+        assert status[jh][0] == 2
+        assert all(status[j][0] == 0 for k, j in enumerate(jobs) if k != 4)
+        assert srv.stats()["peak_bytes"] <= budget
+        assert max_active < len(jobs)
+
+
+def test_poisson_arrival_driver():
+    sp = specs(13) * 3
+    arrivals = serve.poisson_arrivals(200.0, len(sp), 3)
+    with serve.Server(1 << 34) as srv:
+        res, wall = serve.run_arrivals(srv, sp, arrivals, 5)
+    assert len(res) == len(sp) and all(r["status"] == 0 for r in res)
+    assert all(r["latency"] > 0 for r in res)
+    summ = serve.latency_summary(res)
+    assert 0 < summ["p50_s"] <= summ["p99_s"]

@@ -36,3 +36,21 @@ def test_init_factors_exact_in_fp32():
     for A in F:
         assert A.dtype == np.float32 and (A >= 0).all() and (A < 1).all()
         np.testing.assert_array_equal(A.astype(np.float64) * 2**24, np.round(A.astype(np.float64) * 2**24))
+
+
+def test_serving_workloads_distribution():
+    tensors, jobs = synth.serving_workloads(400, pool=40)
+    assert len(tensors) == 40 and len(jobs) == 400
+    for w in tensors:
+        assert w.nmodes in (3, 4)
+        assert all(500 <= d <= 100_000 for d in w.dims)
+        assert 1 <= w.nnz <= 5_000_000
+    assert {r for _, r, _ in jobs} == {16, 32, 64}
+
+
+def test_poisson_arrivals_rate():
+    from paper_2003_03572_gb300 import serve
+
+    a = serve.poisson_arrivals(200.0, 20000, 1)
+    assert (np.diff(a) > 0).all()
+    assert a[-1] / 20000 == pytest.approx(1 / 200.0, rel=0.03)
