@@ -480,6 +480,18 @@ def serve_arm(args):
                 a.iterate(iters)
                 same &= all(np.array_equal(a.factor(n), r["factors"][n]) for n in range(len(sp["dims"])))
     summ = serve.latency_summary(res)
+    base = None
+    if args.serve_baseline:
+        # the same arrival stream served one job at a time with FP32 gathers
+        specs32 = [dict(sp, precision=S.SACD_FP32) for sp in specs]
+        with serve.Server(int(args.budget_gb * 2**30), max_active=1, stream=stream.cuda_stream) as srv1:
+            res1, wall1 = serve.run_arrivals(srv1, specs32, arrivals, iters)
+        ok1 = [r for r in res1 if r["status"] == 0]
+        fit_b = {r["index"]: r["fit"] for r in ok}
+        dfit = [abs(fit_b[r["index"]] - r["fit"]) for r in ok1 if r["index"] in fit_b]
+        base = {"solves_per_s": len(ok1) / wall1, "latency": serve.latency_summary(res1), "wall_s": wall1,
+                "fit_abs_diff_mean": float(np.mean(dfit)) if dfit else None,
+                "fit_abs_diff_max": float(np.max(dfit)) if dfit else None}
     line = {
         "metric": "served SaCD solves/s",
         "value": len(ok) / wall,
@@ -492,6 +504,7 @@ def serve_arm(args):
         "same_alone_and_in_mix": bool(same),
         "peak_device_bytes": st["peak_bytes"],
         "server_steps": st["steps"],
+        "one_at_a_time_fp32": base,
         "config": {"workload": f"Poisson arrivals {args.rate}/s, {len(specs)} jobs, N in {{3,4}}, dims log-uniform "
                                f"[500,100000], nnz log-uniform [50k,5M], Zipf(1.1), R in {{16,32,64}}, BF16 gathers, "
                                f"{iters} iterations, {args.budget_gb} GiB budget, {len(tensors)} distinct tensors",
@@ -524,6 +537,7 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--pool", type=int, default=64)
     ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-baseline", action="store_true", help="also serve the stream one job at a time, FP32")
     args = ap.parse_args()
     if args.cpu_baseline_child:
         cpu_baseline_child(args.workload, args.steps)

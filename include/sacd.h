@@ -69,7 +69,9 @@ typedef struct {
   const float* vals;          /* nnz values (any sign; repeated coordinates are summed) */
   int32_t rank;               /* R, 1 <= R <= 256 */
   const float* const* init;   /* host array of N pointers to I_n x R row-major FP32, or NULL:
-                                 U[0,1) from `seed`. Values must be finite and >= 0 */
+                                 U[0,1) values (h >> 40) * 2^-24 drawn on the device, h the
+                                 splitmix64 finaliser of seed + (n+1)*0xD1B54A32D192ED03 +
+                                 (i*R + r + 1)*0x9E3779B97F4A7C15. Values must be finite, >= 0 */
   uint64_t seed;              /* used only when init == NULL */
   int32_t precision;          /* sacd_precision */
   int32_t lnorm;              /* sacd_lnorm */
@@ -252,7 +254,8 @@ void sacd_batch_destroy(sacd_batch* b);
  * on one GPU, single-threaded API.
  *  - sacd_server_create: `hbm_budget_bytes` caps the device memory of admitted jobs (each job is
  *    charged an upper bound of its create-time peak until it is admitted, then the bytes its
- *    context holds); at most `max_active` jobs run at once; `stream` as for contexts.
+ *    context holds); at most `max_active` jobs run at once and at most `max_admit_per_step` are
+ *    admitted per step; `stream` as for contexts.
  *  - sacd_server_submit: queue a job (FIFO) that will run `iters` outer iterations. The arrays
  *    that cfg points to are read when the job is admitted and must stay valid until its result
  *    has been drained by sacd_server_results. cfg->stream is ignored.
@@ -282,7 +285,8 @@ typedef struct {
   int32_t active, waiting, finished;
   int64_t used_bytes, peak_bytes, budget_bytes, steps;
 } sacd_server_stats_t;
-sacd_status sacd_server_create(int64_t hbm_budget_bytes, int32_t max_active, void* stream, sacd_server** out);
+sacd_status sacd_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t max_admit_per_step,
+                               void* stream, sacd_server** out);
 sacd_status sacd_server_submit(sacd_server* s, const sacd_config* cfg, int32_t iters, int64_t* job_id);
 sacd_status sacd_server_step(sacd_server* s, int32_t* n_active, int32_t* n_waiting);
 sacd_status sacd_server_results(sacd_server* s, sacd_job_result* out, int32_t cap, int32_t* n);

@@ -46,6 +46,9 @@ struct ModeData {
   int64_t nheavy = 0;
   int4* chunks = nullptr;
   int64_t nchunks = 0;
+  int4* split_tmp = nullptr;     // create-time list of split rows (ntiles entries)
+  uint32_t* split_pos = nullptr;
+  uint32_t* split_tot = nullptr;
   // state
   float* A = nullptr;
   __nv_bfloat16* A16 = nullptr;
@@ -132,12 +135,15 @@ sacd_status cuda_fail(sacd_ctx* c, cudaError_t e, const char* where) {
     if (_e != cudaSuccess) return cuda_fail(c, _e, #expr);    \
   } while (0)
 
+// Device allocations come from the device's stream-ordered memory pool (cudaMallocAsync on the
+// context's stream), so that contexts created and destroyed at a high rate (serving) reuse
+// cached memory instead of paying for cudaMalloc/cudaFree each time.
 template <typename T>
 sacd_status dalloc(sacd_ctx* c, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
   void* q = nullptr;
-  const cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  const cudaError_t e = cudaMallocAsync(&q, count * sizeof(T), c->st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(SACD_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
@@ -154,18 +160,20 @@ sacd_status dalloc(sacd_ctx* c, T** p, size_t count) {
     if (_s != SACD_OK) return _s;        \
   } while (0)
 
-// temporaries that are freed at the end of sacd_create
+// temporaries that are freed (stream-ordered) at the end of sacd_create
 struct TmpAllocs {
+  cudaStream_t st;
   std::vector<void*> p;
+  explicit TmpAllocs(cudaStream_t s) : st(s) {}
   ~TmpAllocs() {
-    for (void* q : p) cudaFree(q);
+    for (void* q : p) cudaFreeAsync(q, st);
   }
   template <typename T>
   sacd_status get(T** out, size_t count) {
     *out = nullptr;
     if (count == 0) count = 1;
     void* q = nullptr;
-    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    if (cudaMallocAsync(&q, count * sizeof(T), st) != cudaSuccess) {
       cudaGetLastError();
       return fail(SACD_ENOMEM, "cudaMalloc of temporary " + std::to_string(count * sizeof(T)) + " bytes failed");
     }
@@ -187,12 +195,6 @@ int next_pow2(int x) {
   return p;
 }
 
-uint64_t splitmix64(uint64_t& s) {
-  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
 
 void prof_record(sacd_ctx* c, int cls, bool start) {
   Prof& p = c->prof;
@@ -413,55 +415,70 @@ sacd_status build_mode(sacd_ctx* c, TmpAllocs& T, SortBufs& B, int n, const int3
   md.sub = (int)sub;
   md.tile = (int)(groups * sub);
   md.ntiles = (nnz + md.tile - 1) / md.tile;
-  // rows split across tiles
-  md.nlight = md.nheavy = 0;
+  // rows split across tiles: flags, positions and the list are computed here; the lists of all
+  // modes are read back with one synchronisation in finish_split_lists
+  md.nlight = md.nheavy = md.nchunks = 0;
+  md.split_tmp = nullptr;
+  md.split_tot = nullptr;
   if (md.ntiles > 1) {
-    uint32_t *flags, *pos, *tot;
+    uint32_t* flags;
     void* stmp;
-    int4* lst;
     TRY(T.get(&flags, md.ntiles));
-    TRY(T.get(&pos, md.ntiles));
-    TRY(T.get(&tot, 1));
+    TRY(T.get(&md.split_pos, md.ntiles));
+    TRY(T.get(&md.split_tot, 1));
     TRY(T.get(reinterpret_cast<char**>(&stmp), scan_tmp_bytes(md.ntiles)));  // NOLINT
+    TRY(T.get(&md.split_tmp, md.ntiles));
     launch_split_flags(md.rowid, nnz, md.tile, md.ntiles, flags, c->st);
-    scan_u32(flags, pos, md.ntiles, tot, stmp, c->st);
-    uint32_t h_tot = 0;
-    CK(cudaMemcpyAsync(&h_tot, tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    if (h_tot) {
-      TRY(T.get(&lst, h_tot));
-      launch_split_emit(md.rowid, nnz, md.tile, md.ntiles, flags, pos, lst, c->st);
-      std::vector<int4> h(h_tot);
-      CK(cudaMemcpyAsync(h.data(), lst, sizeof(int4) * h_tot, cudaMemcpyDeviceToHost, c->st));
-      CK(cudaStreamSynchronize(c->st));
-      std::vector<int4> light, heavy, chunks;
-      for (const int4& s : h) {
-        const int64_t P = (int64_t)s.z - s.y + 1;  // partials of the row
-        if (P <= 16) {
-          light.push_back(s);
-        } else {
-          const int first = (int)chunks.size();
-          for (int64_t k0 = 0; k0 < P; k0 += kFixChunk)
-            chunks.push_back(make_int4(s.x, s.y, (int)k0, (int)std::min<int64_t>(kFixChunk, P - k0)));
-          heavy.push_back(make_int4(s.x, first, (int)chunks.size() - first, 0));
-        }
+    scan_u32(flags, md.split_pos, md.ntiles, md.split_tot, stmp, c->st);
+    launch_split_emit(md.rowid, nnz, md.tile, md.ntiles, flags, md.split_pos, md.split_tmp, c->st);
+    CK(cudaGetLastError());
+  }
+  return SACD_OK;
+}
+
+// Light rows (<= 16 partials) are summed by one warp each; heavy rows are cut into chunks of
+// kFixChunk partials (level 1) whose sums are added per row (level 2).
+sacd_status finish_split_lists(sacd_ctx* c) {
+  std::vector<std::vector<int4>> lists(c->N);
+  std::vector<uint32_t> tots(c->N, 0);
+  bool any = false;
+  for (int n = 0; n < c->N; ++n) {
+    ModeData& md = c->m[n];
+    if (!md.split_tmp) continue;
+    any = true;
+    lists[n].resize(md.ntiles);
+    CK(cudaMemcpyAsync(&tots[n], md.split_tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(lists[n].data(), md.split_tmp, sizeof(int4) * md.ntiles, cudaMemcpyDeviceToHost, c->st));
+  }
+  if (any) CK(cudaStreamSynchronize(c->st));
+  for (int n = 0; n < c->N; ++n) {
+    ModeData& md = c->m[n];
+    std::vector<int4> light, heavy, chunks;
+    for (uint32_t i = 0; i < tots[n]; ++i) {
+      const int4 s = lists[n][i];
+      const int64_t P = (int64_t)s.z - s.y + 1;  // partials of the row
+      if (P <= 16) {
+        light.push_back(s);
+      } else {
+        const int first = (int)chunks.size();
+        for (int64_t k0 = 0; k0 < P; k0 += kFixChunk)
+          chunks.push_back(make_int4(s.x, s.y, (int)k0, (int)std::min<int64_t>(kFixChunk, P - k0)));
+        heavy.push_back(make_int4(s.x, first, (int)chunks.size() - first, 0));
       }
-      md.nlight = (int64_t)light.size();
-      md.nheavy = (int64_t)heavy.size();
-      md.nchunks = (int64_t)chunks.size();
-      TRY(dalloc(c, &md.split_light, light.size()));
-      TRY(dalloc(c, &md.split_heavy, heavy.size()));
-      TRY(dalloc(c, &md.chunks, chunks.size()));
-      if (!chunks.empty())
-        CK(cudaMemcpyAsync(md.chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice, c->st));
-      if (!light.empty())
-        CK(cudaMemcpyAsync(md.split_light, light.data(), sizeof(int4) * light.size(), cudaMemcpyHostToDevice,
-                           c->st));
-      if (!heavy.empty())
-        CK(cudaMemcpyAsync(md.split_heavy, heavy.data(), sizeof(int4) * heavy.size(), cudaMemcpyHostToDevice,
-                           c->st));
-      CK(cudaStreamSynchronize(c->st));
     }
+    md.nlight = (int64_t)light.size();
+    md.nheavy = (int64_t)heavy.size();
+    md.nchunks = (int64_t)chunks.size();
+    TRY(dalloc(c, &md.split_light, light.size()));
+    TRY(dalloc(c, &md.split_heavy, heavy.size()));
+    TRY(dalloc(c, &md.chunks, chunks.size()));
+    // pageable host sources: each copy has read its source when it returns
+    if (!chunks.empty())
+      CK(cudaMemcpyAsync(md.chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice, c->st));
+    if (!light.empty())
+      CK(cudaMemcpyAsync(md.split_light, light.data(), sizeof(int4) * light.size(), cudaMemcpyHostToDevice, c->st));
+    if (!heavy.empty())
+      CK(cudaMemcpyAsync(md.split_heavy, heavy.data(), sizeof(int4) * heavy.size(), cudaMemcpyHostToDevice, c->st));
   }
   return SACD_OK;
 }
@@ -506,6 +523,21 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
   c->lnorm = cfg->lnorm;
   c->fixup = cfg->fixup;
   configure_kernels();
+  {
+    // keep freed blocks of the stream-ordered pool cached in this process (a process-local pool
+    // attribute, not a device setting): contexts created and destroyed back to back reuse them
+    static bool pool_done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !pool_done[dev]) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+      cudaGetLastError();
+      pool_done[dev] = true;
+    }
+  }
   if (cfg->stream) {
     c->st = reinterpret_cast<cudaStream_t>(cfg->stream);
   } else {
@@ -525,7 +557,6 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     std::vector<double> st0((size_t)N * ST_STRIDE, 0.0);
     for (int n = 0; n < N; ++n) st0[(size_t)n * ST_STRIDE + ST_FIRST] = 1.0;
     CK(cudaMemcpyAsync(c->state, st0.data(), sizeof(double) * st0.size(), cudaMemcpyHostToDevice, c->st));
-    CK(cudaStreamSynchronize(c->st));
   }
   TRY(dalloc(c, &c->counters, 8));
   CK(cudaMemsetAsync(c->counters, 0, 8 * sizeof(unsigned int), c->st));
@@ -535,7 +566,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
   TRY(dalloc(c, &d_dims, N));
   CK(cudaMemcpyAsync(d_dims, c->dims, sizeof(int64_t) * N, cudaMemcpyHostToDevice, c->st));
 
-  TmpAllocs T;
+  TmpAllocs T(c->st);
   SortBufs B;
   const int64_t nnz_in = cfg->nnz;
   TRY(B.alloc(T, std::max<int64_t>(nnz_in, 1)));
@@ -556,10 +587,14 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
       CK(cudaMemcpyAsync(vals_in, cfg->vals, sizeof(float) * nnz_in, in_kind, c->st));
       launch_validate_idx(idx_in, nnz_in, N, d_dims, nnz_in, bad, c->st);
     }
+    // (an out-of-range coordinate only makes the sort below order garbage keys; it is reported
+    // with the count of distinct coordinates, in one synchronisation)
     unsigned int h_bad = 0;
     CK(cudaMemcpyAsync(&h_bad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    if (h_bad) return fail(SACD_EINVAL, "a coordinate is outside [0, dims[n])");
+    if (nnz_in == 0) {
+      CK(cudaStreamSynchronize(c->st));
+      if (h_bad) return fail(SACD_EINVAL, "a coordinate is outside [0, dims[n])");
+    }
 
     int64_t nnz = 0;
     if (nnz_in > 0) {
@@ -585,6 +620,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
       uint32_t h_tot = 0;
       CK(cudaMemcpyAsync(&h_tot, tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
       CK(cudaStreamSynchronize(c->st));
+      if (h_bad) return fail(SACD_EINVAL, "a coordinate is outside [0, dims[n])");
       nnz = h_tot;
       TRY(T.get(&uidx, (size_t)N * nnz));
       TRY(T.get(&uvals, nnz));
@@ -602,13 +638,13 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
       launch_sumsq(uvals, c->nnz, part, 1024, outp, c->counters + 4, c->st);
       CK(cudaMemcpyAsync(&c->norm_x_sq, outp, sizeof(double), cudaMemcpyDeviceToHost, c->st));
     }
-    CK(cudaStreamSynchronize(c->st));
   }
   // ---- per-mode slice structures
   for (int n = 0; n < N; ++n) {
     c->m[n].I = c->dims[n];
     TRY(build_mode(c, T, B, n, uidx, uvals));
   }
+  TRY(finish_split_lists(c));  // one synchronisation (also completes the ||X||^2 read-back)
   // ---- factors and state
   int64_t Imax = 0, tiles_max = 0, p1_max = 0, gb_max = 0, chunks_max = 0;
   const int RB1 = rows_per_block_pass1(Rp), RB2 = rows_per_block_pass2(Rp);
@@ -643,12 +679,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
       CK(cudaMemcpy2DAsync(md.A, sizeof(float) * Rp, cfg->init[n], sizeof(float) * R, sizeof(float) * R, I, k,
                            c->st));
     } else {
-      std::vector<float> h((size_t)I * Rp, 0.f);
-      uint64_t s = cfg->seed ^ (0xA5A5A5A5ull * (uint64_t)(n + 1));
-      for (int64_t i = 0; i < I; ++i)
-        for (int r = 0; r < R; ++r) h[(size_t)i * Rp + r] = (float)((splitmix64(s) >> 40) * (1.0 / 16777216.0));
-      CK(cudaMemcpyAsync(md.A, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, c->st));
-      CK(cudaStreamSynchronize(c->st));
+      launch_init_factor(md.A, I, R, Rp, cfg->seed, n, c->st);
     }
     if (md.A16) launch_to_bf16(md.A, md.A16, I * Rp, c->st);
   }
@@ -745,7 +776,6 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     {
       const int64_t fb[2] = {0, c->fit_blocks};
       CK(cudaMemcpyAsync(c->fitbase, fb, sizeof(fb), cudaMemcpyHostToDevice, c->st));
-      CK(cudaStreamSynchronize(c->st));
     }
     FitDesc& f = c->hfit;
     memset(&f, 0, sizeof(f));
@@ -1056,7 +1086,8 @@ void sacd_destroy(sacd_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   invalidate_graph(c);
   for (auto& e : c->prof.ev) cudaEventDestroy(e);
-  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->allocs) cudaFreeAsync(p, c->st);
+  if (c->st) cudaStreamSynchronize(c->st);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->side) cudaStreamDestroy(c->side);
@@ -1108,12 +1139,14 @@ struct BatchPlan {
   int64_t fit_blocks = 0;
   double* d_fit_out = nullptr;  // njobs x 4
   std::vector<void*> allocs;
+  cudaStream_t alloc_st = nullptr;
 
   template <typename T>
   sacd_status alloc_copy(T** dst, const std::vector<T>& src, cudaStream_t st) {
     void* q = nullptr;
     const size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
-    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    alloc_st = st;
+    if (cudaMallocAsync(&q, bytes, st) != cudaSuccess) {
       cudaGetLastError();
       return fail(SACD_ENOMEM, "cudaMalloc of a batch plan array failed");
     }
@@ -1125,7 +1158,7 @@ struct BatchPlan {
   }
 
   void release() {
-    for (void* p : allocs) cudaFree(p);
+    for (void* p : allocs) cudaFreeAsync(p, alloc_st);  // after the work already enqueued
     allocs.clear();
   }
 
@@ -1436,6 +1469,7 @@ double now_s(const std::chrono::steady_clock::time_point& t0) {
 struct sacd_server {
   int64_t budget = 0;
   int32_t max_active = 0;
+  int32_t max_admit = 0;
   cudaStream_t st = nullptr;
   bool own_stream = false;
   bool poisoned = false;
@@ -1467,14 +1501,17 @@ void finish_job(sacd_server* s, ServerJob* j) {
 
 extern "C" {
 
-sacd_status sacd_server_create(int64_t hbm_budget_bytes, int32_t max_active, void* stream, sacd_server** out) {
+sacd_status sacd_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t max_admit_per_step,
+                               void* stream, sacd_server** out) {
   if (!out) return fail(SACD_EINVAL, "null out");
   *out = nullptr;
-  if (hbm_budget_bytes <= 0 || max_active < 1) return fail(SACD_EINVAL, "budget and max_active must be positive");
+  if (hbm_budget_bytes <= 0 || max_active < 1 || max_admit_per_step < 1)
+    return fail(SACD_EINVAL, "budget, max_active and max_admit_per_step must be positive");
   sacd_server* s = new (std::nothrow) sacd_server();
   if (!s) return fail(SACD_ENOMEM, "host allocation failed");
   s->budget = hbm_budget_bytes;
   s->max_active = max_active;
+  s->max_admit = max_admit_per_step;
   s->t0 = std::chrono::steady_clock::now();
   if (stream) {
     s->st = reinterpret_cast<cudaStream_t>(stream);
@@ -1523,8 +1560,10 @@ sacd_status sacd_server_submit(sacd_server* s, const sacd_config* cfg, int32_t i
 sacd_status sacd_server_step(sacd_server* s, int32_t* n_active, int32_t* n_waiting) {
   if (!s) return fail(SACD_EINVAL, "null server");
   if (s->poisoned) return fail(SACD_ESTATE, "server is poisoned by an earlier CUDA error");
-  // ---- admission, FIFO, within the budget
-  while (!s->waiting.empty() && (int)s->active.size() < s->max_active) {
+  // ---- admission, FIFO, within the budget, at most max_admit per step (creating a context takes
+  // GPU time too; capping it keeps the admitted jobs iterating while a burst arrives)
+  int admitted = 0;
+  while (!s->waiting.empty() && (int)s->active.size() < s->max_active && admitted < s->max_admit) {
     ServerJob* j = s->waiting.front();
     if (!s->active.empty() && s->used + j->est_bytes > s->budget) break;
     if (j->est_bytes > s->budget) {  // can never fit
@@ -1548,6 +1587,7 @@ sacd_status sacd_server_step(sacd_server* s, int32_t* n_active, int32_t* n_waiti
       }
       continue;
     }
+    ++admitted;
     j->ctx = c;
     j->bytes = c->device_bytes;
     s->used += j->bytes;

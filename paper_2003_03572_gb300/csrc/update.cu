@@ -589,6 +589,29 @@ void launch_to_bf16(const float* src, void* dst, int64_t n, cudaStream_t st) {
   to_bf16_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, reinterpret_cast<__nv_bfloat16*>(dst), n);
 }
 
+// U[0,1) initial factor values (h >> 40) * 2^-24, where h is the splitmix64 finaliser of
+// seed + (mode + 1) * 0xD1B54A32D192ED03 + (element + 1) * 0x9E3779B97F4A7C15 (a counter-based
+// generator: every element is drawn independently, so the draw is the same on any grid).
+__global__ void init_factor_kernel(float* __restrict__ A, int64_t rows, int R, int Rp, unsigned long long seed,
+                                   int mode) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * R;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + (unsigned long long)(mode + 1) * 0xD1B54A32D192ED03ull +
+                           (unsigned long long)(e + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const int64_t i = e / R;
+    const int r = (int)(e - i * R);
+    A[i * Rp + r] = (float)(z >> 40) * (1.0f / 16777216.0f);
+  }
+}
+void launch_init_factor(float* A, int64_t rows, int R, int Rp, unsigned long long seed, int mode, cudaStream_t st) {
+  if (rows * R <= 0) return;
+  const int64_t blocks = min((rows * R + 255) / 256, (int64_t)152 * 16);
+  init_factor_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, rows, R, Rp, seed, mode);
+}
+
 __global__ void check_factor_kernel(const float* __restrict__ A, int64_t rows, int R, int Rp,
                                     unsigned int* bad) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * R;

@@ -174,7 +174,7 @@ def lib():
         "sacd_batch_fit": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(dbl)]),
         "sacd_batch_job": (C.c_int, [vp, i32, C.POINTER(vp)]),
         "sacd_batch_destroy": (None, [vp]),
-        "sacd_server_create": (C.c_int, [i64, i32, vp, C.POINTER(vp)]),
+        "sacd_server_create": (C.c_int, [i64, i32, i32, vp, C.POINTER(vp)]),
         "sacd_server_submit": (C.c_int, [vp, C.POINTER(sacd_config), i32, C.POINTER(i64)]),
         "sacd_server_step": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32)]),
         "sacd_server_results": (C.c_int, [vp, C.POINTER(sacd_job_result), i32, C.POINTER(i32)]),
@@ -513,9 +513,10 @@ class SaCDBatch:
 # ------------------------------------------------------------------------------------ serving
 
 
-def sacd_server_create(hbm_budget_bytes, max_active=1024, stream=None):
+def sacd_server_create(hbm_budget_bytes, max_active=1024, max_admit_per_step=16, stream=None):
     out = C.c_void_p()
-    _check(lib().sacd_server_create(int(hbm_budget_bytes), int(max_active), stream, C.byref(out)))
+    _check(lib().sacd_server_create(int(hbm_budget_bytes), int(max_active), int(max_admit_per_step), stream,
+                                    C.byref(out)))
     return out.value
 
 

@@ -17,8 +17,8 @@ __all__ = ["Server", "poisson_arrivals", "run_arrivals", "latency_summary"]
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes, max_active=1024, stream=None):
-        self.s = S.sacd_server_create(hbm_budget_bytes, max_active, stream)
+    def __init__(self, hbm_budget_bytes, max_active=1024, max_admit_per_step=16, stream=None):
+        self.s = S.sacd_server_create(hbm_budget_bytes, max_active, max_admit_per_step, stream)
         self._keep = {}
         self._shapes = {}
 
