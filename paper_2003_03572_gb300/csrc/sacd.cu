@@ -389,14 +389,21 @@ sacd_status build_mode(sacd_ctx* c, TmpAllocs& T, SortBufs& B, int n, const int3
   ModeData& md = c->m[n];
   const int64_t nnz = c->nnz;
   const int N = c->N;
-  TRY(dalloc(c, &md.rowid, nnz));
-  TRY(dalloc(c, &md.cidx, (size_t)(N - 1) * nnz));
-  TRY(dalloc(c, &md.val, nnz));
+  if (n == 0 && nnz > 0) {
+    // the distinct coordinates are already in mode-0 order (i_0, i_1, ..., i_{N-1}): alias them
+    md.rowid = const_cast<int32_t*>(uidx);
+    md.cidx = const_cast<int32_t*>(uidx) + nnz;
+    md.val = const_cast<float*>(uvals);
+  } else {
+    TRY(dalloc(c, &md.rowid, nnz));
+    TRY(dalloc(c, &md.cidx, (size_t)(N - 1) * nnz));
+    TRY(dalloc(c, &md.val, nnz));
+  }
   std::vector<int> order;
   order.push_back(n);
   for (int k = 0; k < N; ++k)
     if (k != n) order.push_back(k);
-  if (nnz > 0) {
+  if (nnz > 0 && n > 0) {
     uint32_t* perm = nullptr;
     TRY(sort_order(c, B, uidx, nnz, nnz, order, &perm));
     launch_gather_i32(uidx + (int64_t)n * nnz, perm, md.rowid, nnz, c->st);
@@ -622,8 +629,8 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
       CK(cudaStreamSynchronize(c->st));
       if (h_bad) return fail(SACD_EINVAL, "a coordinate is outside [0, dims[n])");
       nnz = h_tot;
-      TRY(T.get(&uidx, (size_t)N * nnz));
-      TRY(T.get(&uvals, nnz));
+      TRY(dalloc(c, &uidx, (size_t)N * nnz));  // kept: mode 0's slice structure
+      TRY(dalloc(c, &uvals, nnz));
       launch_dup_compact(sidx, nnz_in, N, svals, heads, pos, nnz_in, uidx, nnz, uvals, c->st);
       CK(cudaGetLastError());
     }
