@@ -26,9 +26,10 @@
 struct StepDesc {
   // ---- mode-n sorted nonzeros (slice structure)
   const int32_t* rowid;  // nnz: i_n per nonzero, ascending
-  const int32_t* cidx;   // (N-1) x nnz: the other modes' indices, ascending mode order
+  const int32_t* cidx;   // (N-1) rows of cstride: the other modes' indices, ascending mode order
   const float* val;      // nnz
   int64_t nnz;
+  int64_t cstride;       // row stride of cidx (nnz rounded up to a multiple of 4 in a context)
   int32_t nother;        // N-1
   int32_t prec;          // 0: gather FP32 rows, 1: gather BF16 rows
   const void* fac[SACD_MAXN - 1];  // the other factors (FP32 master or BF16 mirror), row stride Rp
@@ -52,7 +53,8 @@ struct StepDesc {
   // ---- update of factor n
   float* A;              // I x Rp FP32 master
   __nv_bfloat16* A16;    // I x Rp BF16 mirror (or null)
-  float* G;              // I x Rp gradient at the start of the step
+  float* G;              // I x Rp gradient at the start of the step (rounded to FP32)
+  float* Glo;            // I x Rp its rounding error: G + Glo carries the compensated sum unrounded
   float* zprev;          // I x Rp z^{k-1}
   uint8_t* mask;         // I x Rp selection record (or null)
   const uint8_t* replay; // I x Rp selection to apply instead (used when state[ST_REPLAY] != 0)

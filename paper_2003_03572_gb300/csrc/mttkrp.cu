@@ -49,13 +49,16 @@ struct WarpPieces {
 };
 
 constexpr int kWarpsPerBlock = 8;
+// Nonzeros whose gathers a lane group issues together, and resident blocks per SM (which bounds
+// the registers), per kernel variant: measured on GB300 (5M-nonzero Zipf R = 32 FP32: 4 and 2,
+// 0.367 ms per iteration against 0.406-0.469 for the other three pairs; 50M-nonzero 4-mode R = 64
+// BF16: 2 and 3, 7.92 ms against 8.60-9.87). Rows of up to 4 floats per lane take the first pair.
 #ifndef SACD_MTTKRP_UNROLL
-#define SACD_MTTKRP_UNROLL 2
+#define SACD_MTTKRP_UNROLL 0
 #endif
 #ifndef SACD_MTTKRP_MINB
-#define SACD_MTTKRP_MINB 3
+#define SACD_MTTKRP_MINB 0
 #endif
-constexpr int kUnroll = SACD_MTTKRP_UNROLL;  // nonzeros whose gathers are issued together
 
 template <int PREC, int RV>
 struct TileShape {
@@ -64,6 +67,8 @@ struct TileShape {
   static constexpr int CPL = RV / LPR;           // vectors per lane
   static constexpr int G = 32 / LPR;             // lane groups per warp
   static constexpr int NV = CPL * W;             // floats per lane
+  static constexpr int U = SACD_MTTKRP_UNROLL ? SACD_MTTKRP_UNROLL : (NV <= 4 ? 4 : 2);
+  static constexpr int MINB = SACD_MTTKRP_MINB ? SACD_MTTKRP_MINB : (NV <= 4 ? 2 : 3);
 };
 
 template <int NV>
@@ -103,6 +108,7 @@ template <int PREC, int RV, int NO>
 __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpPieces& wp) {
   using S = TileShape<PREC, RV>;
   constexpr int MAXO = NO > 0 ? NO : SACD_MAXN - 1;
+  constexpr int kUnroll = S::U;
   const int lane = lane_id();
   const int g = lane / S::LPR;   // group
   const int lig = lane % S::LPR; // lane in group
@@ -117,11 +123,16 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
   const int nother = NO > 0 ? NO : dp->nother;
   const int32_t* ci[MAXO];
   const void* fac[MAXO];
+  const int64_t cstride = dp->cstride;
 #pragma unroll
   for (int m = 0; m < MAXO; ++m) {
-    ci[m] = dp->cidx + (int64_t)m * nnz;
+    ci[m] = dp->cidx + (int64_t)m * cstride;
     fac[m] = dp->fac[m];
   }
+  // 128-bit index loads of 4 consecutive nonzeros when every index row is 16-byte aligned
+  // (tiles and sub-ranges start at multiples of 4 nonzeros)
+  const bool vec = (((reinterpret_cast<uintptr_t>(rowid) | reinterpret_cast<uintptr_t>(val) |
+                      reinterpret_cast<uintptr_t>(dp->cidx)) & 15) == 0) && ((cstride & 3) == 0);
   const int t0 = (int)(tile * tile_nnz);
   const int t1 = min(t0 + tile_nnz, nnz);
   const int a = min(t0 + g * sub, t1);
@@ -165,30 +176,69 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
 
   for (int e0 = a; e0 < b; e0 += kUnroll) {
     int32_t rows[kUnroll];
-    float prod[kUnroll][S::NV];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int e = e0 + u;
-      if (e < b) {
-        rows[u] = __ldg(rowid + e);
-        const float x = __ldg(val + e);
-#pragma unroll
-        for (int i = 0; i < S::NV; ++i) prod[u][i] = x;
+    float xs[kUnroll];
+    uint32_t ix[MAXO][kUnroll];
+    bool loaded = false;
+    if constexpr (kUnroll == 2) {
+      if (vec && e0 + 2 <= b) {
+        const int2 r2 = __ldg(reinterpret_cast<const int2*>(rowid + e0));
+        const float2 x2 = __ldg(reinterpret_cast<const float2*>(val + e0));
+        rows[0] = r2.x; rows[1] = r2.y;
+        xs[0] = x2.x; xs[1] = x2.y;
 #pragma unroll
         for (int m = 0; m < MAXO; ++m) {
           if (NO > 0 || m < nother) {
-            const uint32_t r = (uint32_t)__ldg(ci[m] + e);
+            const int2 c2 = __ldg(reinterpret_cast<const int2*>(ci[m] + e0));
+            ix[m][0] = c2.x; ix[m][1] = c2.y;
+          }
+        }
+        loaded = true;
+      }
+    } else if constexpr (kUnroll == 4) {
+      if (vec && e0 + 4 <= b) {
+        const int4 r4 = __ldg(reinterpret_cast<const int4*>(rowid + e0));
+        const float4 x4 = __ldg(reinterpret_cast<const float4*>(val + e0));
+        rows[0] = r4.x; rows[1] = r4.y; rows[2] = r4.z; rows[3] = r4.w;
+        xs[0] = x4.x; xs[1] = x4.y; xs[2] = x4.z; xs[3] = x4.w;
+#pragma unroll
+        for (int m = 0; m < MAXO; ++m) {
+          if (NO > 0 || m < nother) {
+            const int4 c4 = __ldg(reinterpret_cast<const int4*>(ci[m] + e0));
+            ix[m][0] = c4.x; ix[m][1] = c4.y; ix[m][2] = c4.z; ix[m][3] = c4.w;
+          }
+        }
+        loaded = true;
+      }
+    }
+    if (!loaded) {
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int e = e0 + u;
+        rows[u] = e < b ? __ldg(rowid + e) : -1;
+        xs[u] = e < b ? __ldg(val + e) : 0.f;
+#pragma unroll
+        for (int m = 0; m < MAXO; ++m)
+          if (NO > 0 || m < nother) ix[m][u] = e < b ? (uint32_t)__ldg(ci[m] + e) : 0u;
+      }
+    }
+    float prod[kUnroll][S::NV];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (e0 + u < b) {
+#pragma unroll
+        for (int i = 0; i < S::NV; ++i) prod[u][i] = xs[u];
+#pragma unroll
+        for (int m = 0; m < MAXO; ++m) {
+          if (NO > 0 || m < nother) {
 #pragma unroll
             for (int k = 0; k < S::CPL; ++k) {
               float v[S::W];
-              GatherVec<PREC>::load(fac[m], (int64_t)r * RV + lig + k * S::LPR, v);
+              GatherVec<PREC>::load(fac[m], (int64_t)ix[m][u] * RV + lig + k * S::LPR, v);
 #pragma unroll
               for (int i = 0; i < S::W; ++i) prod[u][k * S::W + i] *= v[i];
             }
           }
         }
-      } else {
-        rows[u] = -1;
       }
     }
 #pragma unroll
@@ -284,10 +334,10 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
   }
 }
 
-// 8 warps per block; SACD_MTTKRP_MINB resident blocks per SM bound the registers, so that
+// 8 warps per block; TileShape::MINB resident blocks per SM bound the registers, so that
 // enough gathers are in flight to cover the L2 latency.
 template <int PREC, int RV, int NO>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, SACD_MTTKRP_MINB)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, (TileShape<PREC, RV>::MINB))
     mttkrp_kernel(const StepDesc* __restrict__ descs, const int64_t* __restrict__ tile_base, int njobs,
                   int64_t total_tiles) {
   __shared__ WarpPieces pieces[kWarpsPerBlock];

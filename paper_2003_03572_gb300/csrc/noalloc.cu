@@ -160,6 +160,7 @@ sacd_status sacd_mttkrp_noalloc(int32_t nmodes, int32_t mode, const int64_t* dim
   d.cidx = cidx;
   d.val = vals;
   d.nnz = nnz;
+  d.cstride = nnz;
   d.nother = nmodes - 1;
   d.prec = 0;
   int o = 0;

@@ -76,6 +76,7 @@ struct sacd_ctx {
   int N = 0;
   int64_t dims[SACD_MAXN] = {0};
   int64_t nnz = 0;
+  int64_t cstride = 0;  // row stride of the index arrays: nnz rounded up to a multiple of 4
   int R = 0, Rp = 0, rv = 0;
   int prec = 0, lnorm = 0, fixup = 0;
   cudaStream_t st = nullptr;
@@ -91,6 +92,7 @@ struct sacd_ctx {
   ModeData m[SACD_MAXN];
   // shared scratch
   float* G = nullptr;
+  float* Glo = nullptr;
   uint8_t* mask = nullptr;
   uint8_t* replay = nullptr;
   float* carry = nullptr;
@@ -392,11 +394,11 @@ sacd_status build_mode(sacd_ctx* c, TmpAllocs& T, SortBufs& B, int n, const int3
   if (n == 0 && nnz > 0) {
     // the distinct coordinates are already in mode-0 order (i_0, i_1, ..., i_{N-1}): alias them
     md.rowid = const_cast<int32_t*>(uidx);
-    md.cidx = const_cast<int32_t*>(uidx) + nnz;
+    md.cidx = const_cast<int32_t*>(uidx) + c->cstride;
     md.val = const_cast<float*>(uvals);
   } else {
     TRY(dalloc(c, &md.rowid, nnz));
-    TRY(dalloc(c, &md.cidx, (size_t)(N - 1) * nnz));
+    TRY(dalloc(c, &md.cidx, (size_t)(N - 1) * c->cstride));
     TRY(dalloc(c, &md.val, nnz));
   }
   std::vector<int> order;
@@ -405,11 +407,12 @@ sacd_status build_mode(sacd_ctx* c, TmpAllocs& T, SortBufs& B, int n, const int3
     if (k != n) order.push_back(k);
   if (nnz > 0 && n > 0) {
     uint32_t* perm = nullptr;
-    TRY(sort_order(c, B, uidx, nnz, nnz, order, &perm));
-    launch_gather_i32(uidx + (int64_t)n * nnz, perm, md.rowid, nnz, c->st);
+    const int64_t cs = c->cstride;
+    TRY(sort_order(c, B, uidx, cs, nnz, order, &perm));
+    launch_gather_i32(uidx + (int64_t)n * cs, perm, md.rowid, nnz, c->st);
     int o = 0;
     for (int k = 0; k < N; ++k)
-      if (k != n) launch_gather_i32(uidx + (int64_t)k * nnz, perm, md.cidx + (int64_t)(o++) * nnz, nnz, c->st);
+      if (k != n) launch_gather_i32(uidx + (int64_t)k * cs, perm, md.cidx + (int64_t)(o++) * cs, nnz, c->st);
     launch_gather_f32(uvals, perm, md.val, nnz, c->st);
     CK(cudaGetLastError());
   }
@@ -629,9 +632,10 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
       CK(cudaStreamSynchronize(c->st));
       if (h_bad) return fail(SACD_EINVAL, "a coordinate is outside [0, dims[n])");
       nnz = h_tot;
-      TRY(dalloc(c, &uidx, (size_t)N * nnz));  // kept: mode 0's slice structure
+      c->cstride = (nnz + 3) / 4 * 4;
+      TRY(dalloc(c, &uidx, (size_t)N * c->cstride));  // kept: mode 0's slice structure
       TRY(dalloc(c, &uvals, nnz));
-      launch_dup_compact(sidx, nnz_in, N, svals, heads, pos, nnz_in, uidx, nnz, uvals, c->st);
+      launch_dup_compact(sidx, nnz_in, N, svals, heads, pos, nnz_in, uidx, c->cstride, uvals, c->st);
       CK(cudaGetLastError());
     }
     c->nnz = nnz;
@@ -701,6 +705,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     if (h_bad) return fail(SACD_EINVAL, "init values must be finite and >= 0");
   }
   TRY(dalloc(c, &c->G, (size_t)Imax * Rp));
+  TRY(dalloc(c, &c->Glo, (size_t)Imax * Rp));
   TRY(dalloc(c, &c->mask, (size_t)Imax * Rp));
   TRY(dalloc(c, &c->replay, (size_t)Imax * Rp));
   TRY(dalloc(c, &c->carry, (size_t)std::max<int64_t>(tiles_max, 1) * 2 * Rp));
@@ -726,6 +731,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     d.cidx = md.cidx;
     d.val = md.val;
     d.nnz = c->nnz;
+    d.cstride = c->cstride;
     d.nother = N - 1;
     d.prec = c->prec;
     int o = 0;
@@ -750,6 +756,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     d.A = md.A;
     d.A16 = md.A16;
     d.G = c->G;
+    d.Glo = c->Glo;
     d.zprev = md.zprev;
     d.mask = nullptr;
     d.replay = c->replay;
@@ -971,8 +978,8 @@ sacd_status sacd_debug_tap(sacd_ctx* c, int32_t what, int32_t mode, void* host_o
       break;
     case SACD_TAP_CSF_IDX:
       if (c->nnz)
-        CK(cudaMemcpyAsync(host_out, md.cidx, sizeof(int32_t) * c->nnz * (c->N - 1), cudaMemcpyDeviceToHost,
-                           c->st));
+        CK(cudaMemcpy2DAsync(host_out, sizeof(int32_t) * c->nnz, md.cidx, sizeof(int32_t) * c->cstride,
+                             sizeof(int32_t) * c->nnz, c->N - 1, cudaMemcpyDeviceToHost, c->st));
       break;
     case SACD_TAP_CSF_VAL:
       if (c->nnz) CK(cudaMemcpyAsync(host_out, md.val, sizeof(float) * c->nnz, cudaMemcpyDeviceToHost, c->st));

@@ -109,7 +109,7 @@ size_t pass_smem_bytes(int Rp) {
   size_t b = (size_t)RB * (Rp + 1) * sizeof(float);  // staged A rows
   if (Rp <= 64) b += (size_t)Rp * Rp * sizeof(float);  // H
   b += (size_t)RB * 32;                                // selection bytes (pass 2)
-  b += (size_t)8 * 2 * Rp * sizeof(float);             // per-warp G and M rows (pass 2)
+  b += (size_t)RB * (Rp + 1) * sizeof(float);          // per-row step history (pass 2)
   return (b + 15) / 16 * 16;
 }
 
@@ -186,21 +186,24 @@ __global__ void __launch_bounds__(256) pass1_kernel(const StepDesc* __restrict__
       dot2_acc(aj, h1.x, hi[4], lo[4]); dot2_acc(aj, h1.y, hi[5], lo[5]);
       dot2_acc(aj, h1.z, hi[6], lo[6]); dot2_acc(aj, h1.w, hi[7], lo[7]);
     }
-    float g[8];
+    float g[8], gl[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      g[u] = __fadd_rn(hi[u], lo[u]);
+      two_sum(hi[u], lo[u], g[u], gl[u]);  // g + gl = hi + lo exactly; g is the rounded value
       const int c = c0 + u;
       if (c < R) {
         const float s = sacd_step(arow[c], g[u], __ldg(invh + c));
         zsum += sacd_importance(g[u], s, __ldg(lh + c));
       } else {
-        g[u] = 0.f;
+        g[u] = gl[u] = 0.f;
       }
     }
     float4* g4 = reinterpret_cast<float4*>(G + row * Rp + c0);
     g4[0] = make_float4(g[0], g[1], g[2], g[3]);
     g4[1] = make_float4(g[4], g[5], g[6], g[7]);
+    float4* gl4 = reinterpret_cast<float4*>(dp->Glo + row * Rp + c0);
+    gl4[0] = make_float4(gl[0], gl[1], gl[2], gl[3]);
+    gl4[1] = make_float4(gl[4], gl[5], gl[6], gl[7]);
   }
   const double bz = block_sum((double)zsum, red);
   if (threadIdx.x == 0) {
@@ -236,11 +239,8 @@ void launch_pass1(const StepDesc* d_descs, const int64_t* d_base, int njobs, int
 
 // ------------------------------------------------------------------------------------------
 // pass 2: phase A (element-parallel): z from the stored gradient, selection, z^{k-1} <- z.
-// phase B (one warp per row that has a selected element): the selected columns in order,
-// s = max(0, u - g/h) - u (Eq. 12-13). With the Gauss-Seidel fix-up the gradient of a column is
-// recomputed from the current row, g = a_cur . H[:, r] - m_r, as a compensated warp dot product
-// (exact products, error-free sums across lanes), so later columns see the exact gradient
-// without an accumulated chain of FP32 roundings.
+// phase B (one thread per row that has a selected element): the selected columns in order,
+// s = max(0, u - g/h) - u (Eq. 12-13), with the gradient fix-up described below.
 __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__ descs,
                                                    const int64_t* __restrict__ base, int njobs) {
   extern __shared__ float4 smem4[];
@@ -253,7 +253,6 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
   const int R = dp->R, Rp = dp->Rp, ST = Rp + 1;
   const int64_t I = dp->I;
   float* __restrict__ A = dp->A;
-  const float* __restrict__ M = dp->M;
   const float* __restrict__ G = dp->G;
   float* __restrict__ zprev = dp->zprev;
   const float* __restrict__ invh = dp->invh;
@@ -265,7 +264,7 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
   float* As = sm;
   float* Hs = sm + RB * ST;
   uint8_t* selb = reinterpret_cast<uint8_t*>(sm + RB * ST + (Rp <= 64 ? Rp * Rp : 0));
-  float* wrow = reinterpret_cast<float*>(selb + RB * 32);  // 8 warps x (G row, M row)
+  float* wrow = reinterpret_cast<float*>(selb + RB * 32);  // RB x (Rp+1) step history
   const float* __restrict__ Hsrc = dp->Hf;
   stage_rows(A + row0 * Rp, As, nrows, Rp);
   if (Rp <= 64) {
@@ -320,26 +319,24 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
   const long long tot = block_sum(count, cred);  // also orders phase A before phase B
   if (threadIdx.x == 0 && tot) atomicAdd(dp->nsel, (unsigned long long)tot);
   if (tot == 0) return;
-  // ---- phase B
-  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  // ---- phase B: one thread per row that has a selected element, its selected columns in order.
+  // With the Gauss-Seidel fix-up the current gradient of column r is
+  //   g_r = (G + Glo)_r + sum over updated columns q < r of s_q H[q][r]
+  // (H symmetric), summed with error-free transformations from the unrounded start-of-step
+  // gradient, so later columns see the exact gradient without a chain of FP32 roundings.
   const bool gs = dp->fixup == 0;
-  const int CPL = Rp > 32 ? Rp / 32 : 1;
   __nv_bfloat16* __restrict__ A16 = dp->A16;
-  for (int r2 = warp; r2 < nrows; r2 += 8) {
+  const float* __restrict__ Glo = dp->Glo;
+  float* shist = wrow;  // RB x (Rp+1): the step s of each updated column of the row
+  for (int r2 = threadIdx.x; r2 < nrows; r2 += blockDim.x) {
+    const uint8_t* rsel = selb + r2 * TPR;
     bool any = false;
-    for (int k = 0; k < TPR; ++k) any |= selb[r2 * TPR + k] != 0;
+    for (int k = 0; k < TPR; ++k) any |= rsel[k] != 0;
     if (!any) continue;
     const int64_t row = row0 + r2;
     float* arow = As + r2 * ST;
-    float* grow = wrow + warp * 2 * Rp;
-    float* mrow = grow + Rp;
-    for (int c = lane; c < Rp; c += 32) {
-      grow[c] = __ldg(G + row * Rp + c);
-      if (gs) mrow[c] = __ldg(M + row * Rp + c);
-    }
-    __syncwarp();
+    float* srow = shist + r2 * ST;
     bool upd = false;
-    const uint8_t* rsel = selb + r2 * TPR;
     for (int w0 = 0; w0 < TPR; w0 += 4) {  // 32 columns per word, selected columns in order
       uint32_t bits = 0;
       for (int k = 0; k < 4 && w0 + k < TPR; ++k) bits |= (uint32_t)rsel[w0 + k] << (8 * k);
@@ -347,45 +344,32 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
         const int r = w0 * 8 + __ffs(bits) - 1;
         bits &= bits - 1u;
         const float ar = arow[r];
-        float g;
+        float g = __ldg(G + row * Rp + r);
         if (gs && upd) {
-          float hi = 0.f, lo = 0.f;
-          for (int k = 0; k < CPL; ++k) {
-            const int j = lane + 32 * k;
-            if (j < R) dot2_acc(arow[j], Hr[r * Rp + j], hi, lo);  // H is symmetric: H[j][r] = H[r][j]
+          float hi = g, lo = __ldg(Glo + row * Rp + r);
+          for (int q = 0; q < r; ++q) {
+            const float sq = srow[q];
+            if (sq != 0.f) dot2_acc(sq, Hr[q * Rp + r], hi, lo);
           }
-#pragma unroll
-          for (int off = 16; off >= 1; off >>= 1) {
-            const float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
-            const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
-            float s2, t2;
-            two_sum(hi, ohi, s2, t2);
-            hi = s2;
-            lo = __fadd_rn(__fadd_rn(lo, olo), t2);
-          }
-          float s2, t2;
-          two_sum(hi, -mrow[r], s2, t2);
-          g = __fadd_rn(s2, __fadd_rn(lo, t2));
-        } else {
-          g = grow[r];
+          g = __fadd_rn(hi, lo);
         }
         const float s = sacd_step(ar, g, __ldg(invh + r));
         if (s != 0.f) {
-          __syncwarp();
-          if (lane == 0) arow[r] = __fadd_rn(ar, s);
-          __syncwarp();
+          if (!upd)
+            for (int q = 0; q < R; ++q) srow[q] = 0.f;
+          arow[r] = __fadd_rn(ar, s);
+          srow[r] = s;
           upd = true;
         }
       }
     }
     if (upd) {
-      for (int c = lane; c < Rp; c += 32) {
+      for (int c = 0; c < Rp; ++c) {
         const float v = arow[c];
         A[row * Rp + c] = v;
         if (A16) A16[row * Rp + c] = __float2bfloat16_rn(v);
       }
     }
-    __syncwarp();
   }
 }
 
