@@ -177,6 +177,15 @@ sacd_status sacd_set_debug(sacd_ctx* ctx, int32_t on);
  */
 sacd_status sacd_replay_mask(sacd_ctx* ctx, int32_t mode, const uint8_t* host_mask);
 
+/*
+ * sacd_set_tiling -- re-cut the MTTKRP warp tiles of `mode`: `sub` nonzeros per lane group
+ * (a multiple of 4 in [4, 1024]; a tile is 32/LPR groups, LPR = 16-byte vectors per gathered
+ * row, at most 32). The default comes from the autotuned table compiled into the library for the
+ * job's shape. Changes the summation order of M (results stay within the MTTKRP tolerance).
+ * Used by the autotuner; waits. Errors: SACD_EINVAL, SACD_ENOMEM, SACD_ECUDA.
+ */
+sacd_status sacd_set_tiling(sacd_ctx* ctx, int32_t mode, int32_t sub);
+
 /* sacd_get_info -- sizes and constants of the context. */
 sacd_status sacd_get_info(sacd_ctx* ctx, sacd_info* out);
 

@@ -38,6 +38,7 @@ def flags(extra=()):
         "-fPIC,-O2",
         "-I" + os.path.join(ROOT, "include"),
         "-I" + CSRC,
+        "-I" + BUILD,
         *extra,
     ]
 
@@ -53,9 +54,35 @@ def _compile(src, verbose, extra):
     return obj, (r.stdout + r.stderr)
 
 
+TUNING = os.path.join(PKG, "tuning.json")
+TUNE_HEADER = os.path.join(BUILD, "tune_table.h")
+
+
+def write_tune_header():
+    """Turn the autotuned table (tuning.json, written by autotune.py on a GB300) into the C header
+    the library compiles in. Without a table the header holds only a sentinel entry."""
+    import json
+
+    rows = []
+    if os.path.exists(TUNING):
+        for e in json.load(open(TUNING))["entries"]:
+            rows.append(f"  {{{int(e['prec'])}, {int(e['rv'])}, {int(e['nother'])}, {int(e['nnz_lo'])}LL, "
+                        f"{int(e['nnz_hi'])}LL, {int(e['sub'])}}},")
+    rows.append("  {-1, 0, 0, 0LL, 0LL, 0},  // sentinel")
+    text = ("// Generated by paper_2003_03572_gb300/build.py from tuning.json (written by autotune.py).\n"
+            "#pragma once\n#include <stdint.h>\n"
+            "struct TuneEntry {\n  int prec, rv, nother;\n  int64_t nnz_lo, nnz_hi;\n  int sub;\n};\n"
+            "static const TuneEntry kTuneTable[] = {\n" + "\n".join(rows) + "\n};\n")
+    old = open(TUNE_HEADER).read() if os.path.exists(TUNE_HEADER) else None
+    if old != text:
+        with open(TUNE_HEADER, "w") as f:
+            f.write(text)
+
+
 def build(verbose=False, extra=()):
     """Compile every CUDA source and link libsacd.so. Returns the library path."""
     os.makedirs(BUILD, exist_ok=True)
+    write_tune_header()
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         results = list(ex.map(lambda s: _compile(s, verbose, extra), SOURCES))
     objs = [o for o, _ in results]

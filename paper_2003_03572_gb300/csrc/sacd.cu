@@ -16,6 +16,7 @@
 #include "sacd.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "tune_table.h"
 
 using namespace sacd;
 
@@ -97,6 +98,7 @@ struct sacd_ctx {
   uint8_t* replay = nullptr;
   float* carry = nullptr;
   float* carry2 = nullptr;
+  int64_t carry_cap = 0, carry2_cap = 0;  // tiles / chunks the two buffers can hold
   double* gpart = nullptr;
   double* H = nullptr;
   float* Hf = nullptr;
@@ -387,6 +389,61 @@ sacd_status sort_order(sacd_ctx* c, SortBufs& B, const int32_t* idx, int64_t str
   return SACD_OK;
 }
 
+// Nonzeros per lane group of a warp tile ("sub"; a tile is 32/LPR groups of sub nonzeros).
+// Taken from the autotuned table (tune_table.h, generated from tuning.json by the build) for the
+// job's own shape: precision, row width, number of other modes, nonzero count; otherwise a rule
+// that aims at several waves of warps over the GPU.
+int choose_sub(const sacd_ctx* c, int n) {
+  (void)n;
+  const int64_t nnz = c->nnz;
+  for (const TuneEntry& t : kTuneTable)
+    if (t.prec == c->prec && t.rv == c->rv && t.nother == c->N - 1 && nnz >= t.nnz_lo && nnz < t.nnz_hi)
+      return t.sub;
+  const int groups = 32 / std::min(c->rv, 32);
+  int64_t sub = nnz / ((int64_t)groups * 152 * 64);
+  sub = std::max<int64_t>(8, std::min<int64_t>(128, sub));
+  return (int)((sub + 3) / 4 * 4);
+}
+
+void drop_alloc(sacd_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  for (size_t i = 0; i < c->allocs.size(); ++i)
+    if (c->allocs[i] == p) {
+      cudaFreeAsync(p, c->st);
+      c->allocs.erase(c->allocs.begin() + i);
+      c->device_bytes -= (int64_t)bytes;
+      return;
+    }
+}
+
+// Warp tiles of mode n and the list of rows split across their borders (flags, positions and the
+// list are computed here; finish_split_lists reads the lists of all modes back at once).
+sacd_status build_tiling(sacd_ctx* c, TmpAllocs& T, int n, int sub) {
+  ModeData& md = c->m[n];
+  const int64_t nnz = c->nnz;
+  const int groups = 32 / std::min(c->rv, 32);
+  md.sub = sub;
+  md.tile = groups * sub;
+  md.ntiles = (nnz + md.tile - 1) / md.tile;
+  md.nlight = md.nheavy = md.nchunks = 0;
+  md.split_tmp = nullptr;
+  md.split_tot = nullptr;
+  if (md.ntiles > 1) {
+    uint32_t* flags;
+    void* stmp;
+    TRY(T.get(&flags, md.ntiles));
+    TRY(T.get(&md.split_pos, md.ntiles));
+    TRY(T.get(&md.split_tot, 1));
+    TRY(T.get(reinterpret_cast<char**>(&stmp), scan_tmp_bytes(md.ntiles)));  // NOLINT
+    TRY(T.get(&md.split_tmp, md.ntiles));
+    launch_split_flags(md.rowid, nnz, md.tile, md.ntiles, flags, c->st);
+    scan_u32(flags, md.split_pos, md.ntiles, md.split_tot, stmp, c->st);
+    launch_split_emit(md.rowid, nnz, md.tile, md.ntiles, flags, md.split_pos, md.split_tmp, c->st);
+    CK(cudaGetLastError());
+  }
+  return SACD_OK;
+}
+
 sacd_status build_mode(sacd_ctx* c, TmpAllocs& T, SortBufs& B, int n, const int32_t* uidx, const float* uvals) {
   ModeData& md = c->m[n];
   const int64_t nnz = c->nnz;
@@ -416,34 +473,7 @@ sacd_status build_mode(sacd_ctx* c, TmpAllocs& T, SortBufs& B, int n, const int3
     launch_gather_f32(uvals, perm, md.val, nnz, c->st);
     CK(cudaGetLastError());
   }
-  // warp tiles
-  const int lpr = std::min(c->rv, 32);
-  const int groups = 32 / lpr;
-  int64_t sub = nnz / ((int64_t)groups * 152 * 64);
-  sub = std::max<int64_t>(8, std::min<int64_t>(128, sub));
-  sub = (sub + 3) / 4 * 4;
-  md.sub = (int)sub;
-  md.tile = (int)(groups * sub);
-  md.ntiles = (nnz + md.tile - 1) / md.tile;
-  // rows split across tiles: flags, positions and the list are computed here; the lists of all
-  // modes are read back with one synchronisation in finish_split_lists
-  md.nlight = md.nheavy = md.nchunks = 0;
-  md.split_tmp = nullptr;
-  md.split_tot = nullptr;
-  if (md.ntiles > 1) {
-    uint32_t* flags;
-    void* stmp;
-    TRY(T.get(&flags, md.ntiles));
-    TRY(T.get(&md.split_pos, md.ntiles));
-    TRY(T.get(&md.split_tot, 1));
-    TRY(T.get(reinterpret_cast<char**>(&stmp), scan_tmp_bytes(md.ntiles)));  // NOLINT
-    TRY(T.get(&md.split_tmp, md.ntiles));
-    launch_split_flags(md.rowid, nnz, md.tile, md.ntiles, flags, c->st);
-    scan_u32(flags, md.split_pos, md.ntiles, md.split_tot, stmp, c->st);
-    launch_split_emit(md.rowid, nnz, md.tile, md.ntiles, flags, md.split_pos, md.split_tmp, c->st);
-    CK(cudaGetLastError());
-  }
-  return SACD_OK;
+  return build_tiling(c, T, n, choose_sub(c, n));
 }
 
 // Light rows (<= 16 partials) are summed by one warp each; heavy rows are cut into chunks of
@@ -463,6 +493,10 @@ sacd_status finish_split_lists(sacd_ctx* c) {
   if (any) CK(cudaStreamSynchronize(c->st));
   for (int n = 0; n < c->N; ++n) {
     ModeData& md = c->m[n];
+    if (!md.split_tmp && md.ntiles > 1) continue;  // not re-tiled in this call
+    md.split_tmp = nullptr;
+    md.split_tot = nullptr;
+    md.split_pos = nullptr;
     std::vector<int4> light, heavy, chunks;
     for (uint32_t i = 0; i < tots[n]; ++i) {
       const int4 s = lists[n][i];
@@ -476,6 +510,9 @@ sacd_status finish_split_lists(sacd_ctx* c) {
         heavy.push_back(make_int4(s.x, first, (int)chunks.size() - first, 0));
       }
     }
+    drop_alloc(c, md.split_light, sizeof(int4) * std::max<int64_t>(md.nlight, 1));
+    drop_alloc(c, md.split_heavy, sizeof(int4) * std::max<int64_t>(md.nheavy, 1));
+    drop_alloc(c, md.chunks, sizeof(int4) * std::max<int64_t>(md.nchunks, 1));
     md.nlight = (int64_t)light.size();
     md.nheavy = (int64_t)heavy.size();
     md.nchunks = (int64_t)chunks.size();
@@ -708,9 +745,11 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
   TRY(dalloc(c, &c->Glo, (size_t)Imax * Rp));
   TRY(dalloc(c, &c->mask, (size_t)Imax * Rp));
   TRY(dalloc(c, &c->replay, (size_t)Imax * Rp));
-  TRY(dalloc(c, &c->carry, (size_t)std::max<int64_t>(tiles_max, 1) * 2 * Rp));
+  c->carry_cap = std::max<int64_t>(tiles_max, 1);
+  c->carry2_cap = std::max<int64_t>(chunks_max, 1);
+  TRY(dalloc(c, &c->carry, (size_t)c->carry_cap * 2 * Rp));
   TRY(dalloc(c, &c->gpart, (size_t)gb_max * Rp * Rp));
-  TRY(dalloc(c, &c->carry2, (size_t)std::max<int64_t>(chunks_max, 1) * Rp));
+  TRY(dalloc(c, &c->carry2, (size_t)c->carry2_cap * Rp));
   TRY(dalloc(c, &c->H, (size_t)Rp * Rp));
   TRY(dalloc(c, &c->Hf, (size_t)Rp * Rp));
   TRY(dalloc(c, &c->invh, Rp));
@@ -1019,6 +1058,49 @@ sacd_status sacd_replay_mask(sacd_ctx* c, int32_t mode, const uint8_t* host_mask
                      c->st));
   CK(cudaStreamSynchronize(c->st));
   return SACD_OK;
+}
+
+sacd_status sacd_set_tiling(sacd_ctx* c, int32_t mode, int32_t sub) {
+  TRY(check_ctx(c));
+  if (mode < 0 || mode >= c->N) return fail(SACD_EINVAL, "mode out of range");
+  if (sub < 4 || sub > 1024 || (sub & 3)) return fail(SACD_EINVAL, "sub must be a multiple of 4 in [4, 1024]");
+  try {
+    {
+      TmpAllocs T(c->st);
+      TRY(build_tiling(c, T, mode, sub));
+      TRY(finish_split_lists(c));
+      CK(cudaStreamSynchronize(c->st));
+    }
+    ModeData& md = c->m[mode];
+    if (md.ntiles > c->carry_cap) {
+      drop_alloc(c, c->carry, sizeof(float) * c->carry_cap * 2 * c->Rp);
+      c->carry_cap = md.ntiles;
+      TRY(dalloc(c, &c->carry, (size_t)c->carry_cap * 2 * c->Rp));
+    }
+    if (md.nchunks > c->carry2_cap) {
+      drop_alloc(c, c->carry2, sizeof(float) * c->carry2_cap * c->Rp);
+      c->carry2_cap = md.nchunks;
+      TRY(dalloc(c, &c->carry2, (size_t)c->carry2_cap * c->Rp));
+    }
+    for (int n = 0; n < c->N; ++n) {
+      StepDesc& d = c->hdesc[n];
+      d.carry = c->carry;
+      d.carry2 = c->carry2;
+    }
+    StepDesc& d = c->hdesc[mode];
+    d.sub = md.sub;
+    d.tile = md.tile;
+    d.ntiles = md.ntiles;
+    d.split_light = md.split_light;
+    d.nsplit_light = md.nlight;
+    d.split_heavy = md.split_heavy;
+    d.nsplit_heavy = md.nheavy;
+    d.fix_chunks = md.chunks;
+    d.nfix_chunks = md.nchunks;
+    return upload_descs(c);
+  } catch (const std::bad_alloc&) {
+    return fail(SACD_ENOMEM, "host allocation failed");
+  }
 }
 
 sacd_status sacd_get_info(sacd_ctx* c, sacd_info* out) {

@@ -36,6 +36,7 @@ __all__ = [
     "sacd_set_debug",
     "sacd_replay_mask",
     "sacd_get_info",
+    "sacd_set_tiling",
     "sacd_sync",
     "sacd_profile_enable",
     "sacd_profile_read",
@@ -165,6 +166,7 @@ def lib():
         "sacd_set_debug": (C.c_int, [vp, i32]),
         "sacd_replay_mask": (C.c_int, [vp, i32, vp]),
         "sacd_get_info": (C.c_int, [vp, C.POINTER(sacd_info)]),
+        "sacd_set_tiling": (C.c_int, [vp, i32, i32]),
         "sacd_sync": (C.c_int, [vp]),
         "sacd_profile_enable": (C.c_int, [vp, i32]),
         "sacd_profile_read": (C.c_int, [vp, C.POINTER(sacd_kernel_stat), i32, C.POINTER(i32)]),
@@ -384,6 +386,10 @@ def sacd_replay_mask(ctx, mode, mask):
         return
     m = np.ascontiguousarray(mask, dtype=np.uint8)
     _check(lib().sacd_replay_mask(ctx, int(mode), m.ctypes.data))
+
+
+def sacd_set_tiling(ctx, mode, sub):
+    _check(lib().sacd_set_tiling(ctx, int(mode), int(sub)))
 
 
 def sacd_sync(ctx):

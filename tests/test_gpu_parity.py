@@ -338,3 +338,20 @@ def test_full_size_zipf_workload_sampled_rows():
             assert (g.factor(n) >= 0).all()
         obj, fit = g.fit()
         assert np.isfinite(obj)
+
+
+@pytest.mark.parametrize("sub", [4, 16, 64, 256])
+def test_retiling_keeps_mttkrp_and_step(sub):
+    dims, nnz, dist, s, R = CASES[1]
+    idx, vals, init = make_case(dims, nnz, dist, s, R)
+    cidx, cvals = O.coalesce(dims, idx, vals)
+    with S.SaCD(dims, idx, vals, R, init) as g:
+        for n in range(3):
+            S.sacd_set_tiling(g.ctx, n, sub)
+            assert S.sacd_get_info(g.ctx)["tile_nnz"][n] == sub * (32 // min(R * 4 // 16, 32))
+        for n in range(3):
+            F = g.factors()
+            g.mode_step(n)
+            assert relerr(g.tap("M", n), O.mttkrp(list(dims), cidx, cvals, F, n)) <= 1e-5
+        g.iterate(2)  # the graph picks up the new tiling
+        assert all((A >= 0).all() for A in g.factors())
