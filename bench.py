@@ -139,6 +139,24 @@ def run_cpu_baseline(workload, nsteps):
     return d["steps"] / d["seconds"], d
 
 
+def aggregate_over_ranks(local_value, ws, device=None, op="max"):
+    """The slowest rank's time (or the sum of a count) over all ranks of the job; with one rank,
+    the value itself. Used for the timed region (max over ranks) of the replicas."""
+    if ws <= 1:
+        return float(local_value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(local_value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replicas_value(units_per_rank, ws, max_seconds):
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest rank's time."""
+    return ws * units_per_rank / max_seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -235,12 +253,8 @@ def ours_arm(args):
     torch.cuda.synchronize(dev)
     barrier()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * args.steps * N / (ms / 1e3)
+    ms = aggregate_over_ranks(e0.elapsed_time(e1), ws, dev)
+    value = replicas_value(args.steps * N, ws, ms / 1e3)
 
     # ---------------------------------------------------------------- per-kernel timing
     S.sacd_profile_enable(g.ctx, True)
@@ -288,12 +302,8 @@ def ours_arm(args):
         t1 = time.perf_counter()
         if rep > 0:  # first solve is a warm-up (allocator, graph instantiation)
             e2e_times.append(t1 - t0)
-    e2e_s = statistics.median(e2e_times)
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = ws * N * iters / e2e_s
+    e2e_s = aggregate_over_ranks(statistics.median(e2e_times), ws, dev)
+    e2e_value = replicas_value(N * iters, ws, e2e_s)
     h2d = int(len(vals) * (4 * N + 4) + sum(a.nbytes for a in init))
     d2h = int(sum(a.nbytes for a in init) + 16)
 
