@@ -186,6 +186,34 @@ sacd_status sacd_replay_mask(sacd_ctx* ctx, int32_t mode, const uint8_t* host_ma
  */
 sacd_status sacd_set_tiling(sacd_ctx* ctx, int32_t mode, int32_t sub);
 
+/*
+ * sacd_rmse -- RMSE of the current model over n test entries, sqrt(sum (x - x_hat)^2 / n)
+ * (Eq. 30), x_hat = sum_r prod_k A_k[i_k, r] (Eq. 8) evaluated in FP64. idx: array of N pointers
+ * to n int32 coordinates each, vals: n FP32; host memory, or device memory if on_device != 0.
+ * Waits. Errors: SACD_EINVAL (a coordinate out of range), SACD_ENOMEM, SACD_ECUDA.
+ */
+sacd_status sacd_rmse(sacd_ctx* ctx, int64_t n, const int32_t* const* idx, const float* vals, int32_t on_device,
+                      double* rmse);
+
+/*
+ * sacd_pattern_distinctiveness -- PD of factor `mode` (Eq. pd): the cosine similarity of its
+ * columns i < r, averaged over the pairs (columns of zero norm left out), from the factor's FP64
+ * Gram. Lower is more distinct. Waits.
+ */
+sacd_status sacd_pattern_distinctiveness(sacd_ctx* ctx, int32_t mode, double* pd);
+
+/*
+ * Checkpoint and resume of the whole SaCD state: the factors, z^{k-1}, ti^{k-1} and the
+ * first-visit flags of every mode (Algorithm 1 needs all of them to continue exactly).
+ * sacd_save with host_buf == NULL stores the size needed in *bytes; otherwise it writes the state
+ * (cap >= that size) and waits. sacd_load restores a state saved from a context of the same
+ * tensor shape, nonzero count and rank (the tensor itself is not saved: create the context from
+ * the same tensor first). A resumed context continues bit-identically to one never interrupted.
+ * Errors: SACD_EINVAL (size, magic, shape mismatch, bad factor values), SACD_ECUDA.
+ */
+sacd_status sacd_save(sacd_ctx* ctx, void* host_buf, size_t cap, size_t* bytes);
+sacd_status sacd_load(sacd_ctx* ctx, const void* host_buf, size_t bytes);
+
 /* sacd_get_info -- sizes and constants of the context. */
 sacd_status sacd_get_info(sacd_ctx* ctx, sacd_info* out);
 

@@ -64,6 +64,9 @@ __all__ = [
     "model_norm_sq",
     "objective",
     "fit_from_objective",
+    "predict",
+    "rmse",
+    "pattern_distinctiveness",
     "SaCDOracle",
 ]
 
@@ -288,6 +291,45 @@ def objective(idx, vals, factors):
 
 def fit_from_objective(f, nx_sq):
     return 1.0 - np.sqrt(max(f, 0.0)) / np.sqrt(nx_sq) if nx_sq > 0 else 0.0
+
+
+# ----------------------------------------------------------------------------------------
+# Evaluation (Sec. 6.2)
+# ----------------------------------------------------------------------------------------
+
+
+def predict(idx, factors):
+    """x_hat at the given coordinates: sum_r prod_k a_k[i_k, r] (Eq. 8)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    R = factors[0].shape[1]
+    p = np.ones((idx.shape[1], R), dtype=np.float64)
+    for k, A in enumerate(factors):
+        p = p * np.asarray(A, dtype=np.float64)[idx[k]]
+    return p.sum(axis=1)
+
+
+def rmse(idx, vals, factors):
+    """RMSE over test entries, sqrt(sum (x - x_hat)^2 / n) (Eq. 30)."""
+    v = np.asarray(vals, dtype=np.float64)
+    if v.size == 0:
+        return 0.0
+    d = v - predict(idx, factors)
+    return float(np.sqrt(np.sum(d * d) / v.size))
+
+
+def pattern_distinctiveness(W):
+    """PD of a factor (Eq. pd): the cosine similarity of columns i < r, averaged over the pairs
+    (the paper reports one number per factor; the mean is the reading taken here). Columns of
+    zero norm have no direction and are left out."""
+    W = np.asarray(W, dtype=np.float64)
+    R = W.shape[1]
+    norms = np.sqrt(np.sum(W * W, axis=0))
+    vals = []
+    for i in range(R):
+        for r in range(i + 1, R):
+            if norms[i] > 0 and norms[r] > 0:
+                vals.append(float(W[:, i] @ W[:, r]) / (norms[i] * norms[r]))
+    return float(np.mean(vals)) if vals else 0.0
 
 
 # ----------------------------------------------------------------------------------------

@@ -38,6 +38,9 @@ void launch_gram_reduce(const StepDesc* d_descs, const int64_t* d_base, int njob
                         cudaStream_t st);
 void launch_fit(const FitDesc* d_fit, const int64_t* d_base, int njobs, int64_t total_blocks, cudaStream_t st);
 void launch_to_bf16(const float* src, void* dst, int64_t n, cudaStream_t st);
+void launch_rmse(const int32_t* idx, const float* vals, int64_t n, const float* const* fac, int N, int R, int Rp,
+                 double* part, int64_t blocks, double* out, unsigned int* counter, cudaStream_t st);
+void launch_pd(const double* gram, int R, int Rp, double* out, cudaStream_t st);
 void launch_init_factor(float* A, int64_t rows, int R, int Rp, unsigned long long seed, int mode, cudaStream_t st);
 void launch_check_factor(const float* A, int64_t rows, int R, int Rp, unsigned int* bad, cudaStream_t st);
 

@@ -1060,6 +1060,148 @@ sacd_status sacd_replay_mask(sacd_ctx* c, int32_t mode, const uint8_t* host_mask
   return SACD_OK;
 }
 
+sacd_status sacd_rmse(sacd_ctx* c, int64_t n, const int32_t* const* idx, const float* vals, int32_t on_device,
+                      double* rmse) {
+  TRY(check_ctx(c));
+  if (n < 0 || n > 2147483647LL || !rmse || (n > 0 && (!idx || !vals))) return fail(SACD_EINVAL, "bad arguments");
+  for (int k = 0; n > 0 && k < c->N; ++k)
+    if (!idx[k]) return fail(SACD_EINVAL, "null idx[k]");
+  try {
+    TmpAllocs T(c->st);
+    int32_t* didx;
+    float* dvals;
+    double *part, *outp;
+    unsigned int *bad, *cnt;
+    const int64_t blocks = std::max<int64_t>(1, (n + 255) / 256);
+    TRY(T.get(&didx, (size_t)c->N * std::max<int64_t>(n, 1)));
+    TRY(T.get(&dvals, std::max<int64_t>(n, 1)));
+    TRY(T.get(&part, blocks));
+    TRY(T.get(&outp, 1));
+    TRY(T.get(&bad, 2));
+    cnt = bad + 1;
+    CK(cudaMemsetAsync(bad, 0, 2 * sizeof(unsigned int), c->st));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (n > 0) {
+      for (int k = 0; k < c->N; ++k)
+        CK(cudaMemcpyAsync(didx + (int64_t)k * n, idx[k], sizeof(int32_t) * n, kind, c->st));
+      CK(cudaMemcpyAsync(dvals, vals, sizeof(float) * n, kind, c->st));
+      int64_t* ddims;
+      TRY(T.get(&ddims, c->N));
+      CK(cudaMemcpyAsync(ddims, c->dims, sizeof(int64_t) * c->N, cudaMemcpyHostToDevice, c->st));
+      launch_validate_idx(didx, n, c->N, ddims, n, bad, c->st);
+    }
+    const float* fac[SACD_MAXN];
+    for (int k = 0; k < c->N; ++k) fac[k] = c->m[k].A;
+    launch_rmse(didx, dvals, n, fac, c->N, c->R, c->Rp, part, blocks, outp, cnt, c->st);
+    unsigned int h_bad = 0;
+    CK(cudaMemcpyAsync(&h_bad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(rmse, outp, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (h_bad) return fail(SACD_EINVAL, "a test coordinate is outside [0, dims[n])");
+  } catch (const std::bad_alloc&) {
+    return fail(SACD_ENOMEM, "host allocation failed");
+  }
+  return SACD_OK;
+}
+
+sacd_status sacd_pattern_distinctiveness(sacd_ctx* c, int32_t mode, double* pd) {
+  TRY(check_ctx(c));
+  if (mode < 0 || mode >= c->N || !pd) return fail(SACD_EINVAL, "bad mode or null output");
+  TmpAllocs T(c->st);
+  double* outp;
+  TRY(T.get(&outp, 1));
+  launch_pd(c->m[mode].gram, c->R, c->Rp, outp, c->st);
+  CK(cudaMemcpyAsync(pd, outp, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return SACD_OK;
+}
+
+// Checkpoint layout (host byte order): "SACDSTv1", int32 N, int32 R, int64 nnz, int64 dims[N];
+// then per mode: double ti^{k-1}, double first-visit flag, float A[I x R], float z^{k-1}[I x R].
+static size_t state_bytes(const sacd_ctx* c) {
+  size_t b = 8 + 4 + 4 + 8 + 8 * (size_t)c->N;
+  for (int n = 0; n < c->N; ++n) b += 16 + 2 * sizeof(float) * (size_t)c->m[n].I * c->R;
+  return b;
+}
+
+sacd_status sacd_save(sacd_ctx* c, void* host_buf, size_t cap, size_t* bytes) {
+  TRY(check_ctx(c));
+  const size_t need = state_bytes(c);
+  if (bytes) *bytes = need;
+  if (!host_buf) return SACD_OK;
+  if (cap < need) return fail(SACD_EINVAL, "buffer smaller than the state (query the size with a NULL buffer)");
+  char* p = reinterpret_cast<char*>(host_buf);
+  memcpy(p, "SACDSTv1", 8);
+  p += 8;
+  const int32_t N = c->N, R = c->R;
+  memcpy(p, &N, 4);
+  memcpy(p + 4, &R, 4);
+  memcpy(p + 8, &c->nnz, 8);
+  memcpy(p + 16, c->dims, 8 * (size_t)N);
+  p += 16 + 8 * (size_t)N;
+  std::vector<double> st((size_t)N * ST_STRIDE);
+  CK(cudaMemcpyAsync(st.data(), c->state, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int n = 0; n < N; ++n) {
+    const double s2[2] = {st[(size_t)n * ST_STRIDE + ST_TIPREV], st[(size_t)n * ST_STRIDE + ST_FIRST]};
+    memcpy(p, s2, 16);
+    p += 16;
+    const size_t mb = sizeof(float) * (size_t)c->m[n].I * R;
+    CK(cudaMemcpy2DAsync(p, sizeof(float) * R, c->m[n].A, sizeof(float) * c->Rp, sizeof(float) * R, c->m[n].I,
+                         cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpy2DAsync(p + mb, sizeof(float) * R, c->m[n].zprev, sizeof(float) * c->Rp, sizeof(float) * R,
+                         c->m[n].I, cudaMemcpyDeviceToHost, c->st));
+    p += 2 * mb;
+  }
+  CK(cudaStreamSynchronize(c->st));
+  return SACD_OK;
+}
+
+sacd_status sacd_load(sacd_ctx* c, const void* host_buf, size_t bytes) {
+  TRY(check_ctx(c));
+  if (!host_buf || bytes < state_bytes(c)) return fail(SACD_EINVAL, "buffer too small for this context's state");
+  const char* p = reinterpret_cast<const char*>(host_buf);
+  if (memcmp(p, "SACDSTv1", 8) != 0) return fail(SACD_EINVAL, "not a SaCD state buffer");
+  int32_t N, R;
+  int64_t nnz;
+  memcpy(&N, p + 8, 4);
+  memcpy(&R, p + 12, 4);
+  memcpy(&nnz, p + 16, 8);
+  if (N != c->N || R != c->R || nnz != c->nnz) return fail(SACD_EINVAL, "state of another tensor or rank");
+  for (int n = 0; n < N; ++n) {
+    int64_t d;
+    memcpy(&d, p + 24 + 8 * n, 8);
+    if (d != c->dims[n]) return fail(SACD_EINVAL, "state of another tensor shape");
+  }
+  p += 24 + 8 * (size_t)N;
+  std::vector<double> st((size_t)N * ST_STRIDE);
+  CK(cudaMemcpyAsync(st.data(), c->state, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int n = 0; n < N; ++n) {
+    double s2[2];
+    memcpy(s2, p, 16);
+    st[(size_t)n * ST_STRIDE + ST_TIPREV] = s2[0];
+    st[(size_t)n * ST_STRIDE + ST_FIRST] = s2[1];
+    p += 16;
+    const size_t mb = sizeof(float) * (size_t)c->m[n].I * R;
+    const float* a = reinterpret_cast<const float*>(p);
+    for (int64_t e = 0; e < c->m[n].I * R; ++e)
+      if (!(a[e] >= 0.f) || !std::isfinite(a[e])) return fail(SACD_EINVAL, "factor values must be finite and >= 0");
+    CK(cudaMemcpy2DAsync(c->m[n].A, sizeof(float) * c->Rp, p, sizeof(float) * R, sizeof(float) * R, c->m[n].I,
+                         cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpy2DAsync(c->m[n].zprev, sizeof(float) * c->Rp, p + mb, sizeof(float) * R, sizeof(float) * R,
+                         c->m[n].I, cudaMemcpyHostToDevice, c->st));
+    if (c->m[n].A16) launch_to_bf16(c->m[n].A, c->m[n].A16, c->m[n].I * c->Rp, c->st);
+    enqueue_gram(c, n);
+    p += 2 * mb;
+  }
+  CK(cudaMemcpyAsync(c->state, st.data(), sizeof(double) * st.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  c->mlast_valid = false;
+  return SACD_OK;
+}
+
 sacd_status sacd_set_tiling(sacd_ctx* c, int32_t mode, int32_t sub) {
   TRY(check_ctx(c));
   if (mode < 0 || mode >= c->N) return fail(SACD_EINVAL, "mode out of range");

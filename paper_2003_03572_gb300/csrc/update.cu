@@ -573,6 +573,97 @@ void launch_to_bf16(const float* src, void* dst, int64_t n, cudaStream_t st) {
   to_bf16_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, reinterpret_cast<__nv_bfloat16*>(dst), n);
 }
 
+// ------------------------------------------------------------------------------------------
+// evaluation: RMSE over test entries (Eq. 30) and pattern distinctiveness (Eq. pd)
+struct EvalDesc {
+  const int32_t* idx;  // N x n (row stride n)
+  const float* vals;   // n
+  int64_t n;
+  const float* fac[SACD_MAXN];
+  int32_t N, R, Rp;
+  double* part;        // per-block partial sums of squared errors
+  double* out;         // [0] RMSE
+  unsigned int* counter;
+};
+
+// x_hat = sum_r prod_k a_k[i_k, r] with the products and the sum in FP64 (evaluation is not on
+// the iteration path; FP64 keeps x - x_hat exact enough when the model fits the entry closely)
+__global__ void __launch_bounds__(256) rmse_kernel(EvalDesc d) {
+  __shared__ double red[256];
+  __shared__ int amlast;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double sq = 0.0;
+  if (e < d.n) {
+    int64_t rowoff[SACD_MAXN];
+    for (int k = 0; k < d.N; ++k) rowoff[k] = (int64_t)d.idx[(int64_t)k * d.n + e] * d.Rp;
+    double xh = 0.0;
+    for (int r = 0; r < d.R; ++r) {
+      double p = 1.0;
+      for (int k = 0; k < d.N; ++k) p *= (double)d.fac[k][rowoff[k] + r];
+      xh += p;
+    }
+    const double diff = (double)d.vals[e] - xh;
+    sq = diff * diff;
+  }
+  const double bs = block_sum(sq, red);
+  if (threadIdx.x == 0) {
+    d.part[blockIdx.x] = bs;
+    __threadfence();
+    amlast = atomicAdd(d.counter, 1u) == gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (amlast) {
+    __threadfence();
+    double s = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(d.part + b);
+    const double tot = block_sum(s, red);
+    if (threadIdx.x == 0) {
+      d.out[0] = d.n > 0 ? sqrt(tot / (double)d.n) : 0.0;
+      *d.counter = 0u;
+    }
+  }
+}
+
+// mean over column pairs i < r of gram_ir / sqrt(gram_ii gram_rr), columns of zero norm left out
+__global__ void __launch_bounds__(256) pd_kernel(const double* __restrict__ gram, int R, int Rp, double* out) {
+  __shared__ double red[256];
+  __shared__ double cnt[256];
+  double s = 0.0, c = 0.0;
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int i = e / R, r = e - (e / R) * R;
+    if (i < r) {
+      const double gi = gram[i * Rp + i], gr = gram[r * Rp + r];
+      if (gi > 0.0 && gr > 0.0) {
+        s += gram[i * Rp + r] / sqrt(gi * gr);
+        c += 1.0;
+      }
+    }
+  }
+  const double ts = block_sum(s, red);
+  const double tc = block_sum(c, cnt);
+  if (threadIdx.x == 0) out[0] = tc > 0 ? ts / tc : 0.0;
+}
+
+void launch_rmse(const int32_t* idx, const float* vals, int64_t n, const float* const* fac, int N, int R, int Rp,
+                 double* part, int64_t blocks, double* out, unsigned int* counter, cudaStream_t st) {
+  EvalDesc d;
+  d.idx = idx;
+  d.vals = vals;
+  d.n = n;
+  for (int k = 0; k < SACD_MAXN; ++k) d.fac[k] = k < N ? fac[k] : nullptr;
+  d.N = N;
+  d.R = R;
+  d.Rp = Rp;
+  d.part = part;
+  d.out = out;
+  d.counter = counter;
+  rmse_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(d);
+}
+
+void launch_pd(const double* gram, int R, int Rp, double* out, cudaStream_t st) {
+  pd_kernel<<<1, 256, 0, st>>>(gram, R, Rp, out);
+}
+
 // U[0,1) initial factor values (h >> 40) * 2^-24, where h is the splitmix64 finaliser of
 // seed + (mode + 1) * 0xD1B54A32D192ED03 + (element + 1) * 0x9E3779B97F4A7C15 (a counter-based
 // generator: every element is drawn independently, so the draw is the same on any grid).

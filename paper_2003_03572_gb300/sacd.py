@@ -37,6 +37,10 @@ __all__ = [
     "sacd_replay_mask",
     "sacd_get_info",
     "sacd_set_tiling",
+    "sacd_rmse",
+    "sacd_pattern_distinctiveness",
+    "sacd_save",
+    "sacd_load",
     "sacd_sync",
     "sacd_profile_enable",
     "sacd_profile_read",
@@ -167,6 +171,10 @@ def lib():
         "sacd_replay_mask": (C.c_int, [vp, i32, vp]),
         "sacd_get_info": (C.c_int, [vp, C.POINTER(sacd_info)]),
         "sacd_set_tiling": (C.c_int, [vp, i32, i32]),
+        "sacd_rmse": (C.c_int, [vp, i64, C.POINTER(vp), vp, i32, C.POINTER(dbl)]),
+        "sacd_pattern_distinctiveness": (C.c_int, [vp, i32, C.POINTER(dbl)]),
+        "sacd_save": (C.c_int, [vp, vp, C.c_size_t, C.POINTER(C.c_size_t)]),
+        "sacd_load": (C.c_int, [vp, vp, C.c_size_t]),
         "sacd_sync": (C.c_int, [vp]),
         "sacd_profile_enable": (C.c_int, [vp, i32]),
         "sacd_profile_read": (C.c_int, [vp, C.POINTER(sacd_kernel_stat), i32, C.POINTER(i32)]),
@@ -392,6 +400,42 @@ def sacd_set_tiling(ctx, mode, sub):
     _check(lib().sacd_set_tiling(ctx, int(mode), int(sub)))
 
 
+def sacd_rmse(ctx, idx, vals, on_device=False):
+    """RMSE (Eq. 30) of the current model over test entries (idx: N arrays, vals)."""
+    N = len(idx)
+    if on_device:
+        arrs, v = list(idx), vals
+        n = int(v.numel())
+    else:
+        arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in idx]
+        v = np.ascontiguousarray(vals, dtype=np.float32)
+        n = int(v.shape[0])
+    ptrs = (C.c_void_p * N)(*[_ptr(a) for a in arrs])
+    out = C.c_double()
+    _check(lib().sacd_rmse(ctx, n, ptrs, _ptr(v) if n else None, 1 if on_device else 0, C.byref(out)))
+    return out.value
+
+
+def sacd_pattern_distinctiveness(ctx, mode):
+    out = C.c_double()
+    _check(lib().sacd_pattern_distinctiveness(ctx, int(mode), C.byref(out)))
+    return out.value
+
+
+def sacd_save(ctx):
+    """The full SaCD state (factors, z^{k-1}, ti^{k-1}, first-visit flags) as bytes."""
+    n = C.c_size_t()
+    _check(lib().sacd_save(ctx, None, 0, C.byref(n)))
+    buf = (C.c_char * n.value)()
+    _check(lib().sacd_save(ctx, buf, n.value, C.byref(n)))
+    return bytes(buf)
+
+
+def sacd_load(ctx, state):
+    buf = C.create_string_buffer(state, len(state))
+    _check(lib().sacd_load(ctx, buf, len(state)))
+
+
 def sacd_sync(ctx):
     _check(lib().sacd_sync(ctx))
 
@@ -450,6 +494,18 @@ class SaCD:
 
     def tap(self, what, mode=0, last_mode=None):
         return sacd_debug_tap(self.ctx, what, mode, last_mode)
+
+    def rmse(self, idx, vals, on_device=False):
+        return sacd_rmse(self.ctx, idx, vals, on_device)
+
+    def pattern_distinctiveness(self, mode):
+        return sacd_pattern_distinctiveness(self.ctx, mode)
+
+    def save(self):
+        return sacd_save(self.ctx)
+
+    def load(self, state):
+        sacd_load(self.ctx, state)
 
     def set_debug(self, on):
         sacd_set_debug(self.ctx, on)

@@ -362,3 +362,27 @@ def test_round_bf16_against_torch_and_hand_values():
     x = (rng.random(100_000) * 10.0 ** rng.integers(-8, 8, 100_000)).astype(np.float32)
     ref = torch.from_numpy(x).bfloat16().float().numpy().astype(np.float64)
     np.testing.assert_array_equal(O.round_bf16(x), ref)
+
+
+def test_rmse_against_dense_reconstruction():
+    dims, R, nnz, seed = CASES[1]
+    idx, vals, F = random_case(dims, R, nnz, seed)
+    Xh = reconstruct(F)
+    want = np.sqrt(np.mean([(float(vals[e]) - Xh[tuple(idx[:, e])]) ** 2 for e in range(nnz)]))
+    assert O.rmse(idx, vals, F) == pytest.approx(want, rel=1e-13)
+    assert O.rmse(np.zeros((4, 0), np.int64), np.zeros(0), F) == 0.0
+
+
+def test_pattern_distinctiveness_special_cases():
+    scipy = pytest.importorskip("scipy.spatial.distance")
+    I = np.eye(6)[:, :4]  # orthogonal columns
+    assert O.pattern_distinctiveness(I) == 0.0
+    same = np.ones((5, 3))  # identical columns
+    assert O.pattern_distinctiveness(same) == pytest.approx(1.0, abs=1e-15)
+    rng = np.random.default_rng(2)
+    W = rng.random((40, 5))
+    pairs = [1 - scipy.cosine(W[:, i], W[:, r]) for i in range(5) for r in range(i + 1, 5)]
+    assert O.pattern_distinctiveness(W) == pytest.approx(np.mean(pairs), rel=1e-13)
+    W[:, 2] = 0  # a zero column has no direction
+    pairs = [1 - scipy.cosine(W[:, i], W[:, r]) for i in (0, 1, 3, 4) for r in (0, 1, 3, 4) if i < r]
+    assert O.pattern_distinctiveness(W) == pytest.approx(np.mean(pairs), rel=1e-13)
