@@ -239,7 +239,7 @@ void launch_pass1(const StepDesc* d_descs, const int64_t* d_base, int njobs, int
 
 // ------------------------------------------------------------------------------------------
 // pass 2: phase A (element-parallel): z from the stored gradient, selection, z^{k-1} <- z.
-// phase B (one thread per row that has a selected element): the selected columns in order,
+// phase B (the lanes of a row that has a selected element): the selected columns in order,
 // s = max(0, u - g/h) - u (Eq. 12-13), with the gradient fix-up described below.
 __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__ descs,
                                                    const int64_t* __restrict__ base, int njobs) {
@@ -319,55 +319,84 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
   const long long tot = block_sum(count, cred);  // also orders phase A before phase B
   if (threadIdx.x == 0 && tot) atomicAdd(dp->nsel, (unsigned long long)tot);
   if (tot == 0) return;
-  // ---- phase B: one thread per row that has a selected element, its selected columns in order.
-  // With the Gauss-Seidel fix-up the current gradient of column r is
-  //   g_r = (G + Glo)_r + sum over updated columns q < r of s_q H[q][r]
-  // (H symmetric), summed with error-free transformations from the unrounded start-of-step
-  // gradient, so later columns see the exact gradient without a chain of FP32 roundings.
+  // ---- phase B: the TPR lanes of a row (the phase-A layout) update its selected columns in
+  // order. With the Gauss-Seidel fix-up the current gradient of column r is
+  //   g_r = (G + Glo)_r + sum over updated columns q < r of s_q H[r][q]
+  // (H symmetric): each lane sums its own 8 columns q with error-free transformations, the lanes
+  // combine their (hi, lo) partials with a butterfly (every lane ends with the same sum), and the
+  // start-of-step gradient enters unrounded, so later columns see the exact gradient without a
+  // chain of FP32 roundings. Every lane computes the same step; the lane owning column r stores it.
   const bool gs = dp->fixup == 0;
   __nv_bfloat16* __restrict__ A16 = dp->A16;
   const float* __restrict__ Glo = dp->Glo;
   float* shist = wrow;  // RB x (Rp+1): the step s of each updated column of the row
-  for (int r2 = threadIdx.x; r2 < nrows; r2 += blockDim.x) {
-    const uint8_t* rsel = selb + r2 * TPR;
+  if (rl < nrows) {
+    const uint8_t* rsel = selb + rl * TPR;
     bool any = false;
     for (int k = 0; k < TPR; ++k) any |= rsel[k] != 0;
-    if (!any) continue;
-    const int64_t row = row0 + r2;
-    float* arow = As + r2 * ST;
-    float* srow = shist + r2 * ST;
-    bool upd = false;
-    for (int w0 = 0; w0 < TPR; w0 += 4) {  // 32 columns per word, selected columns in order
-      uint32_t bits = 0;
-      for (int k = 0; k < 4 && w0 + k < TPR; ++k) bits |= (uint32_t)rsel[w0 + k] << (8 * k);
-      while (bits) {
-        const int r = w0 * 8 + __ffs(bits) - 1;
-        bits &= bits - 1u;
-        const float ar = arow[r];
-        float g = __ldg(G + row * Rp + r);
-        if (gs && upd) {
-          float hi = g, lo = __ldg(Glo + row * Rp + r);
-          for (int q = 0; q < r; ++q) {
-            const float sq = srow[q];
-            if (sq != 0.f) dot2_acc(sq, Hr[q * Rp + r], hi, lo);
+    if (any) {
+      // lanes of this row: TPR consecutive lanes, aligned (TPR divides 32)
+      const int lane = lane_id();
+      const unsigned gmask = (TPR == 32) ? 0xffffffffu : (((1u << TPR) - 1u) << (lane & ~(TPR - 1)));
+      const int64_t row = row0 + rl;
+      float* arow = As + rl * ST;
+      float* srow = shist + rl * ST;
+      bool upd = false;
+      for (int w0 = 0; w0 < TPR; w0 += 4) {  // 32 columns per word, selected columns in order
+        uint32_t bits = 0;
+        for (int k = 0; k < 4 && w0 + k < TPR; ++k) bits |= (uint32_t)rsel[w0 + k] << (8 * k);
+        while (bits) {
+          const int r = w0 * 8 + __ffs(bits) - 1;
+          bits &= bits - 1u;
+          const float ar = arow[r];
+          float g = __ldg(G + row * Rp + r);
+          if (gs && upd) {
+            float hi = 0.f, lo = 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int q = c0 + u;
+              if (q < r) {
+                const float sq = srow[q];
+                if (sq != 0.f) dot2_acc(sq, Hr[r * Rp + q], hi, lo);
+              }
+            }
+            for (int off = TPR >> 1; off >= 1; off >>= 1) {
+              const float ohi = __shfl_xor_sync(gmask, hi, off, TPR);
+              const float olo = __shfl_xor_sync(gmask, lo, off, TPR);
+              float s2, t2;
+              two_sum(hi, ohi, s2, t2);
+              hi = s2;
+              lo = __fadd_rn(__fadd_rn(lo, olo), t2);
+            }
+            float s2, t2;
+            two_sum(g, hi, s2, t2);
+            g = __fadd_rn(s2, __fadd_rn(__fadd_rn(t2, lo), __ldg(Glo + row * Rp + r)));
           }
-          g = __fadd_rn(hi, lo);
-        }
-        const float s = sacd_step(ar, g, __ldg(invh + r));
-        if (s != 0.f) {
-          if (!upd)
-            for (int q = 0; q < R; ++q) srow[q] = 0.f;
-          arow[r] = __fadd_rn(ar, s);
-          srow[r] = s;
-          upd = true;
+          const float s = sacd_step(ar, g, __ldg(invh + r));
+          if (s != 0.f) {
+            if (!upd) {
+#pragma unroll
+              for (int u = 0; u < 8; ++u) srow[c0 + u] = 0.f;
+            }
+            __syncwarp(gmask);
+            if ((r >> 3) == ch) {
+              arow[r] = __fadd_rn(ar, s);
+              srow[r] = s;
+            }
+            __syncwarp(gmask);
+            upd = true;
+          }
         }
       }
-    }
-    if (upd) {
-      for (int c = 0; c < Rp; ++c) {
-        const float v = arow[c];
-        A[row * Rp + c] = v;
-        if (A16) A16[row * Rp + c] = __float2bfloat16_rn(v);
+      if (upd) {
+        // this lane's 8 columns of the row
+        float4* a4 = reinterpret_cast<float4*>(A + row * Rp + c0);
+        a4[0] = make_float4(arow[c0], arow[c0 + 1], arow[c0 + 2], arow[c0 + 3]);
+        a4[1] = make_float4(arow[c0 + 4], arow[c0 + 5], arow[c0 + 6], arow[c0 + 7]);
+        if (A16) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) A16[row * Rp + c0 + u] = __float2bfloat16_rn(arow[c0 + u]);
+        }
       }
     }
   }
