@@ -109,7 +109,7 @@ size_t pass_smem_bytes(int Rp) {
   size_t b = (size_t)RB * (Rp + 1) * sizeof(float);  // staged A rows
   if (Rp <= 64) b += (size_t)Rp * Rp * sizeof(float);  // H
   b += (size_t)RB * 32;                                // selection bytes (pass 2)
-  b += (size_t)RB * (Rp + 1) * sizeof(float);          // per-row step history (pass 2)
+  b += (size_t)2 * Rp * sizeof(float);                 // 1/h_rr and L/2 (pass 2)
   return (b + 15) / 16 * 16;
 }
 
@@ -264,12 +264,17 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
   float* As = sm;
   float* Hs = sm + RB * ST;
   uint8_t* selb = reinterpret_cast<uint8_t*>(sm + RB * ST + (Rp <= 64 ? Rp * Rp : 0));
-  float* wrow = reinterpret_cast<float*>(selb + RB * 32);  // RB x (Rp+1) step history
+  float* ihs = reinterpret_cast<float*>(selb + RB * 32);    // Rp: 1/h_rr
+  float* lhs = ihs + Rp;                                     // Rp: L/2
   const float* __restrict__ Hsrc = dp->Hf;
   stage_rows(A + row0 * Rp, As, nrows, Rp);
   if (Rp <= 64) {
     for (int e = threadIdx.x; e < Rp * Rp / 4; e += blockDim.x)
       reinterpret_cast<float4*>(Hs)[e] = __ldg(reinterpret_cast<const float4*>(Hsrc) + e);
+  }
+  for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
+    ihs[c] = __ldg(invh + c);
+    lhs[c] = __ldg(lh + c);
   }
   const float* Hr = Rp <= 64 ? Hs : Hsrc;
   __syncthreads();
@@ -277,6 +282,9 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
   const bool replay = dp->state[ST_REPLAY] != 0.0;
   const int rl = threadIdx.x / TPR, ch = threadIdx.x % TPR, c0 = ch * 8;
   long long count = 0;
+  float gv[8];  // this lane's 8 gradient entries of its row, kept for phase B
+#pragma unroll
+  for (int u = 0; u < 8; ++u) gv[u] = 0.f;
   // ---- phase A
   if (rl < nrows) {
     const int64_t row = row0 + rl;
@@ -285,7 +293,8 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
       const float4* g4 = reinterpret_cast<const float4*>(G + row * Rp + c0);
       float4* z4 = reinterpret_cast<float4*>(zprev + row * Rp + c0);
       const float4 ga = g4[0], gb4 = g4[1], za = z4[0], zb = z4[1];
-      const float gv[8] = {ga.x, ga.y, ga.z, ga.w, gb4.x, gb4.y, gb4.z, gb4.w};
+      gv[0] = ga.x; gv[1] = ga.y; gv[2] = ga.z; gv[3] = ga.w;
+      gv[4] = gb4.x; gv[5] = gb4.y; gv[6] = gb4.z; gv[7] = gb4.w;
       const float zp[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
       float zn[8];
 #pragma unroll
@@ -294,8 +303,8 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
         zn[u] = zp[u];
         if (c < R) {
           const float a = As[rl * ST + c];
-          const float s0 = sacd_step(a, gv[u], __ldg(invh + c));
-          const float z = sacd_importance(gv[u], s0, __ldg(lh + c));
+          const float s0 = sacd_step(a, gv[u], ihs[c]);
+          const float z = sacd_importance(gv[u], s0, lhs[c]);
           bool sel;
           if (replay) sel = dp->replay[row * Rp + c] != 0;
           else if (branch == 0) sel = z > 0.f;                    // first visit: z > 0
@@ -319,85 +328,96 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
   const long long tot = block_sum(count, cred);  // also orders phase A before phase B
   if (threadIdx.x == 0 && tot) atomicAdd(dp->nsel, (unsigned long long)tot);
   if (tot == 0) return;
-  // ---- phase B: the TPR lanes of a row (the phase-A layout) update its selected columns in
-  // order. With the Gauss-Seidel fix-up the current gradient of column r is
-  //   g_r = (G + Glo)_r + sum over updated columns q < r of s_q H[r][q]
-  // (H symmetric): each lane sums its own 8 columns q with error-free transformations, the lanes
-  // combine their (hi, lo) partials with a butterfly (every lane ends with the same sum), and the
-  // start-of-step gradient enters unrounded, so later columns see the exact gradient without a
-  // chain of FP32 roundings. Every lane computes the same step; the lane owning column r stores it.
-  const bool gs = dp->fixup == 0;
+  // ---- phase B. Each lane keeps its 8 columns of the row (the phase-A layout).
   __nv_bfloat16* __restrict__ A16 = dp->A16;
-  const float* __restrict__ Glo = dp->Glo;
-  float* shist = wrow;  // RB x (Rp+1): the step s of each updated column of the row
-  if (rl < nrows) {
+  const int64_t row = row0 + rl;
+  float* arow = As + rl * ST;
+  bool dirty = false;  // this lane changed one of its own columns
+  if (dp->fixup != 0) {
+    // Lemma 2: every selected element steps from the start-of-step gradient, independently.
+    if (rl < nrows && c0 < R) {
+      const unsigned bits = selb[rl * TPR + ch];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if ((bits >> u) & 1u) {
+          const int c = c0 + u;
+          const float a = arow[c];
+          arow[c] = __fadd_rn(a, sacd_step(a, gv[u], ihs[c]));
+          dirty = true;
+        }
+    }
+  } else {
+    // Column Gauss-Seidel: the selected columns of the row in order; the current gradient of
+    // column r is
+    //   g_r = (G + Glo)_r + sum over updated columns q < r of s_q H[q][r].
+    // When column q moves by s_q, every lane adds s_q H[q][c] to a compensated (hi, lo)
+    // accumulator of each of its own columns c (error-free products and sums), so g_r is the
+    // exact start-of-step gradient plus an exactly accumulated correction, rounded once. The
+    // warp walks the union of its rows' selected columns with uniform control flow (each row
+    // applies only its own selections), so its rows never serialise on divergent paths.
+    float glv[8], ahi[8], alo[8];
+    const float* __restrict__ Glo = dp->Glo;
     const uint8_t* rsel = selb + rl * TPR;
-    bool any = false;
-    for (int k = 0; k < TPR; ++k) any |= rsel[k] != 0;
-    if (any) {
-      // lanes of this row: TPR consecutive lanes, aligned (TPR divides 32)
-      const int lane = lane_id();
-      const unsigned gmask = (TPR == 32) ? 0xffffffffu : (((1u << TPR) - 1u) << (lane & ~(TPR - 1)));
-      const int64_t row = row0 + rl;
-      float* arow = As + rl * ST;
-      float* srow = shist + rl * ST;
-      bool upd = false;
-      for (int w0 = 0; w0 < TPR; w0 += 4) {  // 32 columns per word, selected columns in order
-        uint32_t bits = 0;
-        for (int k = 0; k < 4 && w0 + k < TPR; ++k) bits |= (uint32_t)rsel[w0 + k] << (8 * k);
-        while (bits) {
-          const int r = w0 * 8 + __ffs(bits) - 1;
-          bits &= bits - 1u;
-          const float ar = arow[r];
-          float g = __ldg(G + row * Rp + r);
-          if (gs && upd) {
-            float hi = 0.f, lo = 0.f;
+    const bool live = rl < nrows;
+    if (live) {
+      const float4* gl4 = reinterpret_cast<const float4*>(Glo + row * Rp + c0);
+      const float4 la = __ldg(gl4), lb2 = __ldg(gl4 + 1);
+      glv[0] = la.x; glv[1] = la.y; glv[2] = la.z; glv[3] = la.w;
+      glv[4] = lb2.x; glv[5] = lb2.y; glv[6] = lb2.z; glv[7] = lb2.w;
+    } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int q = c0 + u;
-              if (q < r) {
-                const float sq = srow[q];
-                if (sq != 0.f) dot2_acc(sq, Hr[r * Rp + q], hi, lo);
-              }
-            }
-            for (int off = TPR >> 1; off >= 1; off >>= 1) {
-              const float ohi = __shfl_xor_sync(gmask, hi, off, TPR);
-              const float olo = __shfl_xor_sync(gmask, lo, off, TPR);
-              float s2, t2;
-              two_sum(hi, ohi, s2, t2);
-              hi = s2;
-              lo = __fadd_rn(__fadd_rn(lo, olo), t2);
-            }
-            float s2, t2;
-            two_sum(g, hi, s2, t2);
-            g = __fadd_rn(s2, __fadd_rn(__fadd_rn(t2, lo), __ldg(Glo + row * Rp + r)));
-          }
-          const float s = sacd_step(ar, g, __ldg(invh + r));
-          if (s != 0.f) {
-            if (!upd) {
+      for (int u = 0; u < 8; ++u) glv[u] = 0.f;
+    }
 #pragma unroll
-              for (int u = 0; u < 8; ++u) srow[c0 + u] = 0.f;
-            }
-            __syncwarp(gmask);
-            if ((r >> 3) == ch) {
-              arow[r] = __fadd_rn(ar, s);
-              srow[r] = s;
-            }
-            __syncwarp(gmask);
-            upd = true;
+    for (int u = 0; u < 8; ++u) ahi[u] = alo[u] = 0.f;
+    for (int w0 = 0; w0 < TPR; w0 += 4) {  // 32 columns per word, in order
+      uint32_t rowbits = 0;
+      if (live)
+        for (int k = 0; k < 4 && w0 + k < TPR; ++k) rowbits |= (uint32_t)rsel[w0 + k] << (8 * k);
+      uint32_t wbits = __reduce_or_sync(0xffffffffu, rowbits);
+      while (wbits) {
+        const int b = __ffs(wbits) - 1;
+        wbits &= wbits - 1u;
+        const int r = w0 * 8 + b, ur = r & 7;
+        // the owner lane's current gradient of column r, broadcast to its row's lanes
+        float g0 = gv[0], gl0 = glv[0], h0 = ahi[0], l0 = alo[0];
+#pragma unroll
+        for (int u = 1; u < 8; ++u)
+          if (ur == u) {
+            g0 = gv[u];
+            gl0 = glv[u];
+            h0 = ahi[u];
+            l0 = alo[u];
           }
+        float s2, t2;
+        two_sum(g0, h0, s2, t2);
+        const float gown = __fadd_rn(s2, __fadd_rn(__fadd_rn(t2, l0), gl0));
+        const float g = __shfl_sync(0xffffffffu, gown, r >> 3, TPR);
+        const float ar = arow[r];
+        const float s = ((rowbits >> b) & 1u) ? sacd_step(ar, g, ihs[r]) : 0.f;
+        if (s != 0.f) {
+          if ((r >> 3) == ch) {
+            arow[r] = __fadd_rn(ar, s);
+            dirty = true;
+          }
+          const float4 hq0 = *reinterpret_cast<const float4*>(Hr + r * Rp + c0);
+          const float4 hq1 = *reinterpret_cast<const float4*>(Hr + r * Rp + c0 + 4);
+          dot2_acc(s, hq0.x, ahi[0], alo[0]); dot2_acc(s, hq0.y, ahi[1], alo[1]);
+          dot2_acc(s, hq0.z, ahi[2], alo[2]); dot2_acc(s, hq0.w, ahi[3], alo[3]);
+          dot2_acc(s, hq1.x, ahi[4], alo[4]); dot2_acc(s, hq1.y, ahi[5], alo[5]);
+          dot2_acc(s, hq1.z, ahi[6], alo[6]); dot2_acc(s, hq1.w, ahi[7], alo[7]);
         }
       }
-      if (upd) {
-        // this lane's 8 columns of the row
-        float4* a4 = reinterpret_cast<float4*>(A + row * Rp + c0);
-        a4[0] = make_float4(arow[c0], arow[c0 + 1], arow[c0 + 2], arow[c0 + 3]);
-        a4[1] = make_float4(arow[c0 + 4], arow[c0 + 5], arow[c0 + 6], arow[c0 + 7]);
-        if (A16) {
+    }
+  }
+  if (dirty) {
+    // this lane's 8 columns of the row
+    float4* a4 = reinterpret_cast<float4*>(A + row * Rp + c0);
+    a4[0] = make_float4(arow[c0], arow[c0 + 1], arow[c0 + 2], arow[c0 + 3]);
+    a4[1] = make_float4(arow[c0 + 4], arow[c0 + 5], arow[c0 + 6], arow[c0 + 7]);
+    if (A16) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) A16[row * Rp + c0 + u] = __float2bfloat16_rn(arow[c0 + u]);
-        }
-      }
+      for (int u = 0; u < 8; ++u) A16[row * Rp + c0 + u] = __float2bfloat16_rn(arow[c0 + u]);
     }
   }
 }
