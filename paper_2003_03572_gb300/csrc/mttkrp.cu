@@ -49,6 +49,24 @@ struct WarpPieces {
 };
 
 constexpr int kWarpsPerBlock = 8;
+
+// Index staging: a warp copies the next kStageNnz nonzeros' (row, value, other-mode indices) of
+// its lane groups into shared memory with 16-byte asynchronous copies while it gathers and
+// multiplies the current ones, so the DRAM latency of the sorted-nonzero stream overlaps the L2
+// latency of the factor-row gathers. Two stages per warp; completion is the hardware's
+// cp.async group wait (no spin loop). Copies of fewer than 16 valid bytes read only the valid
+// bytes and zero-fill the rest, so nothing past a lane group's range is read.
+#ifndef SACD_MTTKRP_STAGED
+#define SACD_MTTKRP_STAGED 1
+#endif
+constexpr int kStageNnz = 64;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 // Nonzeros whose gathers a lane group issues together, and resident blocks per SM (which bounds
 // the registers), per kernel variant: measured on GB300 (5M-nonzero Zipf R = 32 FP32: 4 and 2,
 // 0.367 ms per iteration against 0.406-0.469 for the other three pairs; 50M-nonzero 4-mode R = 64
@@ -105,7 +123,7 @@ __device__ void zero_rows(float* __restrict__ Mout, int Rp, int64_t r0, int64_t 
 // One warp tile. NO = number of other modes (N-1) when known at compile time, 0 = any.
 // Element positions fit in 32 bits (nnz <= 2^31 - 1); addresses are formed in 64 bits.
 template <int PREC, int RV, int NO>
-__device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpPieces& wp) {
+__device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpPieces& wp, int32_t* sbuf) {
   using S = TileShape<PREC, RV>;
   constexpr int MAXO = NO > 0 ? NO : SACD_MAXN - 1;
   constexpr int kUnroll = S::U;
@@ -174,57 +192,12 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
     }
   };
 
-  for (int e0 = a; e0 < b; e0 += kUnroll) {
-    int32_t rows[kUnroll];
-    float xs[kUnroll];
-    uint32_t ix[MAXO][kUnroll];
-    bool loaded = false;
-    if constexpr (kUnroll == 2) {
-      if (vec && e0 + 2 <= b) {
-        const int2 r2 = __ldg(reinterpret_cast<const int2*>(rowid + e0));
-        const float2 x2 = __ldg(reinterpret_cast<const float2*>(val + e0));
-        rows[0] = r2.x; rows[1] = r2.y;
-        xs[0] = x2.x; xs[1] = x2.y;
-#pragma unroll
-        for (int m = 0; m < MAXO; ++m) {
-          if (NO > 0 || m < nother) {
-            const int2 c2 = __ldg(reinterpret_cast<const int2*>(ci[m] + e0));
-            ix[m][0] = c2.x; ix[m][1] = c2.y;
-          }
-        }
-        loaded = true;
-      }
-    } else if constexpr (kUnroll == 4) {
-      if (vec && e0 + 4 <= b) {
-        const int4 r4 = __ldg(reinterpret_cast<const int4*>(rowid + e0));
-        const float4 x4 = __ldg(reinterpret_cast<const float4*>(val + e0));
-        rows[0] = r4.x; rows[1] = r4.y; rows[2] = r4.z; rows[3] = r4.w;
-        xs[0] = x4.x; xs[1] = x4.y; xs[2] = x4.z; xs[3] = x4.w;
-#pragma unroll
-        for (int m = 0; m < MAXO; ++m) {
-          if (NO > 0 || m < nother) {
-            const int4 c4 = __ldg(reinterpret_cast<const int4*>(ci[m] + e0));
-            ix[m][0] = c4.x; ix[m][1] = c4.y; ix[m][2] = c4.z; ix[m][3] = c4.w;
-          }
-        }
-        loaded = true;
-      }
-    }
-    if (!loaded) {
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int e = e0 + u;
-        rows[u] = e < b ? __ldg(rowid + e) : -1;
-        xs[u] = e < b ? __ldg(val + e) : 0.f;
-#pragma unroll
-        for (int m = 0; m < MAXO; ++m)
-          if (NO > 0 || m < nother) ix[m][u] = e < b ? (uint32_t)__ldg(ci[m] + e) : 0u;
-      }
-    }
+  // gathers, products and row accumulation of the nonzeros e0 .. e0+kUnroll-1 below `lim`
+  auto consume = [&](int e0, const int32_t* rows, const float* xs, const uint32_t (*ix)[kUnroll], int lim) {
     float prod[kUnroll][S::NV];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      if (e0 + u < b) {
+      if (e0 + u < lim) {
 #pragma unroll
         for (int i = 0; i < S::NV; ++i) prod[u][i] = xs[u];
 #pragma unroll
@@ -244,7 +217,7 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int e = e0 + u;
-      if (e < b) {
+      if (e < lim) {
         if (rows[u] != cur) {
           if (cur >= 0) close_seg(cur, seg, e);
           // rows strictly between the previous nonzero's row and this one are empty
@@ -258,6 +231,123 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
 #pragma unroll
         for (int i = 0; i < S::NV; ++i) acc[i] += prod[u][i];
       }
+    }
+  };
+
+  bool staged = false;
+  if constexpr (SACD_MTTKRP_STAGED && (NO == 2 || NO == 3)) staged = vec && (sub & 3) == 0;
+  if constexpr (SACD_MTTKRP_STAGED && (NO == 2 || NO == 3)) {
+   if (staged) {
+    constexpr int NA = 2 + NO;  // staged arrays: rows, values, other-mode indices
+    constexpr int C = kStageNnz / S::G;         // nonzeros per lane group per stage
+    constexpr int QPG = C / 4;                  // 16-byte pieces per lane group and array
+    constexpr int NQ = NA * S::G * QPG;         // pieces per stage
+    constexpr int SLOT = NA * S::G * C;         // int32 words per stage
+    const int32_t* cidx0 = dp->cidx;
+    const int nch = (sub + C - 1) / C;
+    auto issue = [&](int k) {
+      int32_t* dst0 = sbuf + (k & 1) * SLOT;
+      for (int q = lane; q < NQ; q += 32) {
+        const int m = q / (S::G * QPG);
+        const int r = q - m * (S::G * QPG);
+        const int gg = r / QPG, p = r - gg * QPG;
+        const int ag = min(t0 + gg * sub, t1), bg = min(ag + sub, t1);
+        const int e = ag + k * C + 4 * p;
+        const int valid = max(0, min(4, bg - e));
+        const int32_t* arr = m == 0 ? rowid
+                           : (m == 1 ? reinterpret_cast<const int32_t*>(val) : cidx0 + (int64_t)(m - 2) * cstride);
+        cp_async16(dst0 + (m * S::G + gg) * C + 4 * p, valid > 0 ? arr + e : arr, valid * 4);
+      }
+      cp_async_commit();
+    };
+    issue(0);
+    for (int k = 0; k < nch; ++k) {
+      if (k + 1 < nch) issue(k + 1); else cp_async_commit();  // one group per chunk, possibly empty
+      cp_async_wait1();
+      __syncwarp();
+      const int32_t* sb = sbuf + (k & 1) * SLOT;
+      const int cs = a + k * C, ce = min(cs + C, b);
+      for (int e0 = cs; e0 < ce; e0 += kUnroll) {
+        const int o = e0 - cs;
+        int32_t rows[kUnroll];
+        float xs[kUnroll];
+        uint32_t ix[MAXO][kUnroll];
+        // o is a multiple of kUnroll and every array row starts 16-byte aligned
+        if constexpr (kUnroll == 4) {
+          const int4 r4 = *reinterpret_cast<const int4*>(sb + (0 * S::G + g) * C + o);
+          const int4 x4 = *reinterpret_cast<const int4*>(sb + (1 * S::G + g) * C + o);
+          rows[0] = r4.x; rows[1] = r4.y; rows[2] = r4.z; rows[3] = r4.w;
+          xs[0] = __int_as_float(x4.x); xs[1] = __int_as_float(x4.y);
+          xs[2] = __int_as_float(x4.z); xs[3] = __int_as_float(x4.w);
+#pragma unroll
+          for (int m = 0; m < MAXO; ++m) {
+            const int4 c4 = *reinterpret_cast<const int4*>(sb + ((2 + m) * S::G + g) * C + o);
+            ix[m][0] = c4.x; ix[m][1] = c4.y; ix[m][2] = c4.z; ix[m][3] = c4.w;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            rows[u] = sb[(0 * S::G + g) * C + o + u];
+            xs[u] = __int_as_float(sb[(1 * S::G + g) * C + o + u]);
+#pragma unroll
+            for (int m = 0; m < MAXO; ++m) ix[m][u] = (uint32_t)sb[((2 + m) * S::G + g) * C + o + u];
+          }
+        }
+        consume(e0, rows, xs, ix, ce);
+      }
+      __syncwarp();  // the slot is refilled by the next issue
+    }
+   }
+  }
+  if (!staged) {
+    for (int e0 = a; e0 < b; e0 += kUnroll) {
+      int32_t rows[kUnroll];
+      float xs[kUnroll];
+      uint32_t ix[MAXO][kUnroll];
+      bool loaded = false;
+      if constexpr (kUnroll == 2) {
+        if (vec && e0 + 2 <= b) {
+          const int2 r2 = __ldg(reinterpret_cast<const int2*>(rowid + e0));
+          const float2 x2 = __ldg(reinterpret_cast<const float2*>(val + e0));
+          rows[0] = r2.x; rows[1] = r2.y;
+          xs[0] = x2.x; xs[1] = x2.y;
+#pragma unroll
+          for (int m = 0; m < MAXO; ++m) {
+            if (NO > 0 || m < nother) {
+              const int2 c2 = __ldg(reinterpret_cast<const int2*>(ci[m] + e0));
+              ix[m][0] = c2.x; ix[m][1] = c2.y;
+            }
+          }
+          loaded = true;
+        }
+      } else if constexpr (kUnroll == 4) {
+        if (vec && e0 + 4 <= b) {
+          const int4 r4 = __ldg(reinterpret_cast<const int4*>(rowid + e0));
+          const float4 x4 = __ldg(reinterpret_cast<const float4*>(val + e0));
+          rows[0] = r4.x; rows[1] = r4.y; rows[2] = r4.z; rows[3] = r4.w;
+          xs[0] = x4.x; xs[1] = x4.y; xs[2] = x4.z; xs[3] = x4.w;
+#pragma unroll
+          for (int m = 0; m < MAXO; ++m) {
+            if (NO > 0 || m < nother) {
+              const int4 c4 = __ldg(reinterpret_cast<const int4*>(ci[m] + e0));
+              ix[m][0] = c4.x; ix[m][1] = c4.y; ix[m][2] = c4.z; ix[m][3] = c4.w;
+            }
+          }
+          loaded = true;
+        }
+      }
+      if (!loaded) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int e = e0 + u;
+          rows[u] = e < b ? __ldg(rowid + e) : -1;
+          xs[u] = e < b ? __ldg(val + e) : 0.f;
+#pragma unroll
+          for (int m = 0; m < MAXO; ++m)
+            if (NO > 0 || m < nother) ix[m][u] = e < b ? (uint32_t)__ldg(ci[m] + e) : 0u;
+        }
+      }
+      consume(e0, rows, xs, ix, b);
     }
   }
   if (cur >= 0) {
@@ -341,11 +431,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (TileShape<PREC, RV>::MIN
     mttkrp_kernel(const StepDesc* __restrict__ descs, const int64_t* __restrict__ tile_base, int njobs,
                   int64_t total_tiles) {
   __shared__ WarpPieces pieces[kWarpsPerBlock];
+  constexpr int kSlot = (2 + (NO > 0 ? NO : 1)) * kStageNnz;
+  __shared__ __align__(16) int32_t stage[kWarpsPerBlock][(SACD_MTTKRP_STAGED && (NO == 2 || NO == 3)) ? 2 * kSlot : 4];
   const int warp = threadIdx.x >> 5;
   const int64_t gt = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
   if (gt >= total_tiles) return;
   const int j = njobs > 1 ? find_job(tile_base, njobs, gt) : 0;
-  mttkrp_tile<PREC, RV, NO>(descs + j, gt - tile_base[j], pieces[warp]);
+  mttkrp_tile<PREC, RV, NO>(descs + j, gt - tile_base[j], pieces[warp], stage[warp]);
 }
 
 // Rows split across tiles, with few partials: one warp per row, partials summed in tile order.

@@ -24,6 +24,8 @@ from oracle import sacd_oracle as O
 from paper_2003_03572_gb300 import sacd as S
 from paper_2003_03572_gb300 import synth
 
+from fp32_bounds import z_fp32_bound
+
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -112,7 +114,8 @@ def test_mttkrp_gram_and_mode_step_replay(case):
                 assert np.linalg.norm(Gg - t["G"]) / den <= 1e-5
                 zg = g.tap("ZPREV", n)
                 zs = max(np.abs(t["Z"]).max(), 1e-30)
-                assert np.abs(zg - t["Z"]).max() / zs <= 1e-5
+                # 1e-5 of max |z|, widened per element by the FP32 evaluation bound of Eq. 11-12, 20
+                assert (np.abs(zg - t["Z"]) <= 1e-5 * zs + z_fp32_bound(F[n], t)).all()
                 An = g.factor(n)
                 assert (An >= 0).all()
                 assert relerr(An, o.A[n]) <= 1e-5
@@ -130,7 +133,8 @@ def test_mttkrp_gram_and_mode_step_replay(case):
                     else:
                         sp = (t["Zprev"] - t["Z"]) if t["ti"] > t["tiprev"] else (t["Z"] - t["Zprev"])
                     ti_close = abs(t["ti"] - t["tiprev"]) <= 1e-6 * np.abs(t["Z"]).sum()
-                    assert ti_close or np.abs(sp[dis]).max() <= 1e-5 * zs
+                    zb = z_fp32_bound(F[n], t)
+                    assert ti_close or (np.abs(sp[dis]) <= 1e-5 * zs + zb[dis]).all()
 
 
 @pytest.mark.parametrize("lnorm,fixup", [(S.SACD_LNORM_SPECTRAL, 0), (S.SACD_LNORM_GCD, 0), (0, S.SACD_FIXUP_LEMMA2)])
@@ -156,7 +160,7 @@ def test_variants_replay(lnorm, fixup):
                 if lnorm != 2:
                     assert g.tap("STATE", n)[4] == pytest.approx(t["L"], rel=1e-9)
                 zs = max(np.abs(t["Z"]).max(), 1e-30)
-                assert np.abs(g.tap("ZPREV", n) - t["Z"]).max() / zs <= 1e-5
+                assert (np.abs(g.tap("ZPREV", n) - t["Z"]) <= 1e-5 * zs + z_fp32_bound(F[n], t)).all()
                 assert relerr(g.factor(n), o.A[n]) <= 1e-5
 
 
