@@ -48,10 +48,13 @@ struct WarpPieces {
   int32_t flags[32];     // bit0 head valid (left-open), bit1 head also right-open, bit2 tail valid
 };
 
-constexpr int kWarpsPerBlock = 8;
+#ifndef SACD_MTTKRP_WARPS
+#define SACD_MTTKRP_WARPS 4
+#endif
+constexpr int kWarpsPerBlock = SACD_MTTKRP_WARPS;
 
-// Index staging: a warp copies the next kStageNnz nonzeros' (row, value, other-mode indices) of
-// its lane groups into shared memory with 16-byte asynchronous copies while it gathers and
+// Index staging: a warp copies its lane groups' next nonzeros (row, value, other-mode indices)
+// into shared memory with 16-byte asynchronous copies while it gathers and
 // multiplies the current ones, so the DRAM latency of the sorted-nonzero stream overlaps the L2
 // latency of the factor-row gathers. Two stages per warp; completion is the hardware's
 // cp.async group wait (no spin loop). Copies of fewer than 16 valid bytes read only the valid
@@ -59,7 +62,9 @@ constexpr int kWarpsPerBlock = 8;
 #ifndef SACD_MTTKRP_STAGED
 #define SACD_MTTKRP_STAGED 1
 #endif
-constexpr int kStageNnz = 64;
+#ifndef SACD_MTTKRP_STAGE_NNZ
+#define SACD_MTTKRP_STAGE_NNZ 0
+#endif
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -67,10 +72,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-// Nonzeros whose gathers a lane group issues together, and resident blocks per SM (which bounds
-// the registers), per kernel variant: measured on GB300 (5M-nonzero Zipf R = 32 FP32: 4 and 2,
-// 0.367 ms per iteration against 0.406-0.469 for the other three pairs; 50M-nonzero 4-mode R = 64
-// BF16: 2 and 3, 7.92 ms against 8.60-9.87). Rows of up to 4 floats per lane take the first pair.
+// Nonzeros whose gathers a lane group issues together, resident warps per SM (which bound the
+// registers) and index-stage size, per kernel variant, measured on GB300: rows of up to 4 floats
+// per lane (5M-nonzero Zipf R = 32 FP32) 4 nonzeros, 16 warps, 128-nonzero stages; wider rows
+// (50M-nonzero 4-mode R = 64 BF16) 2 nonzeros, 24 warps, 64-nonzero stages. The other pairs
+// measured 5-30% slower.
 #ifndef SACD_MTTKRP_UNROLL
 #define SACD_MTTKRP_UNROLL 0
 #endif
@@ -86,7 +92,14 @@ struct TileShape {
   static constexpr int G = 32 / LPR;             // lane groups per warp
   static constexpr int NV = CPL * W;             // floats per lane
   static constexpr int U = SACD_MTTKRP_UNROLL ? SACD_MTTKRP_UNROLL : (NV <= 4 ? 4 : 2);
-  static constexpr int MINB = SACD_MTTKRP_MINB ? SACD_MTTKRP_MINB : (NV <= 4 ? 2 : 3);
+  // resident warps per SM: 16 for rows of up to 4 floats per lane, 24 for wider ones
+  static constexpr int MINB = SACD_MTTKRP_MINB ? SACD_MTTKRP_MINB : (NV <= 4 ? 16 : 24) / kWarpsPerBlock;
+  // nonzeros of a warp in one index stage (measured: 128 for the narrow rows, 64 for the wide
+  // ones), and per lane group: whole 16-byte pieces and whole unroll steps
+  static constexpr int SNNZ = SACD_MTTKRP_STAGE_NNZ ? SACD_MTTKRP_STAGE_NNZ : (NV <= 4 ? 128 : 64);
+  static constexpr int SMIN = U > 4 ? U : 4;
+  static constexpr int SC = SNNZ / G > SMIN ? SNNZ / G : SMIN;
+  __host__ __device__ static constexpr int stage_words(int nother) { return (2 + nother) * G * SC; }
 };
 
 template <int NV>
@@ -239,10 +252,11 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
   if constexpr (SACD_MTTKRP_STAGED && (NO == 2 || NO == 3)) {
    if (staged) {
     constexpr int NA = 2 + NO;  // staged arrays: rows, values, other-mode indices
-    constexpr int C = kStageNnz / S::G;         // nonzeros per lane group per stage
+    constexpr int C = S::SC;                    // nonzeros per lane group per stage
     constexpr int QPG = C / 4;                  // 16-byte pieces per lane group and array
     constexpr int NQ = NA * S::G * QPG;         // pieces per stage
-    constexpr int SLOT = NA * S::G * C;         // int32 words per stage
+    constexpr int SLOT = S::stage_words(NA - 2);  // int32 words per stage
+    static_assert(C % 4 == 0 && C % kUnroll == 0, "a stage holds whole 16-byte pieces and unroll steps");
     const int32_t* cidx0 = dp->cidx;
     const int nch = (sub + C - 1) / C;
     auto issue = [&](int k) {
@@ -431,7 +445,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (TileShape<PREC, RV>::MIN
     mttkrp_kernel(const StepDesc* __restrict__ descs, const int64_t* __restrict__ tile_base, int njobs,
                   int64_t total_tiles) {
   __shared__ WarpPieces pieces[kWarpsPerBlock];
-  constexpr int kSlot = (2 + (NO > 0 ? NO : 1)) * kStageNnz;
+  constexpr int kSlot = TileShape<PREC, RV>::stage_words(NO > 0 ? NO : 1);
   __shared__ __align__(16) int32_t stage[kWarpsPerBlock][(SACD_MTTKRP_STAGED && (NO == 2 || NO == 3)) ? 2 * kSlot : 4];
   const int warp = threadIdx.x >> 5;
   const int64_t gt = (int64_t)blockIdx.x * kWarpsPerBlock + warp;

@@ -251,6 +251,24 @@ def test_bf16_gather_mode():
         assert abs(g.fit()[1] - o.fit()[1]) <= 5e-3
 
 
+@pytest.mark.parametrize("prec", [S.SACD_FP32, S.SACD_BF16_GATHER], ids=["fp32", "bf16"])
+@pytest.mark.parametrize("R", [1, 8, 12, 32, 100, 256])
+@pytest.mark.parametrize("dims", [(150, 90, 60), (60, 50, 40, 30)], ids=["n3", "n4"])
+def test_mttkrp_every_row_width(dims, R, prec):
+    """Every gathered-row width (one 16-byte vector for R <= 8 with BF16 gathers up to 64 for
+    R = 256 FP32), so every kernel specialisation and index-stage shape runs: M of every mode
+    against the oracle (FP32 gathers) or the oracle's BF16-gather definition, within 1e-5."""
+    idx, vals, init = make_case(dims, 9_001, "zipf", 1.2, R)
+    cidx, cvals = O.coalesce(dims, idx, vals)
+    with S.SaCD(dims, idx, vals, R, init, precision=prec) as g:
+        g.set_debug(True)
+        for n in range(len(dims)):
+            F = g.factors()
+            g.mode_step(n)
+            Fg = F if prec == S.SACD_FP32 else [O.round_bf16(f) for f in F]
+            assert relerr(g.tap("M", n), O.mttkrp(list(dims), cidx, cvals, Fg, n)) <= 1e-5
+
+
 def test_edge_cases():
     # no nonzeros
     with S.SaCD((5, 4, 3), np.zeros((3, 0), np.int32), np.zeros(0, np.float32), 3, seed=1) as g:
