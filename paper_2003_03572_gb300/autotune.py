@@ -25,19 +25,21 @@ from . import sacd as S
 from . import synth
 
 SUBS = (8, 16, 32, 64, 128, 256)
-BUCKETS = ((0, 150_000), (150_000, 1_500_000), (1_500_000, 2**31))
+BUCKETS = ((0, 150_000), (150_000, 1_500_000), (1_500_000, 15_000_000), (15_000_000, 2**31))
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
 
 
 def shapes(quick=False):
     out = []
-    nnzs = (50_000, 500_000, 5_000_000) if not quick else (50_000, 500_000)
+    nnzs = (50_000, 500_000, 5_000_000, 20_000_000) if not quick else (50_000, 500_000)
     for R in (8, 16, 32, 64):
         for N in (3, 4):
             for prec in (S.SACD_FP32, S.SACD_BF16_GATHER):
                 if prec == S.SACD_BF16_GATHER and R < 16:
                     continue
                 for nnz in nnzs:
+                    if nnz > 5_000_000 and R < 32:  # the largest bucket only for the wide ranks
+                        continue
                     if N == 3:
                         dims = (max(1000, nnz // 40), max(500, nnz // 100), 300)
                     else:
