@@ -272,6 +272,7 @@ def ours_arm(args):
     traffic = traffic_from_profile(src_sha)
     kernel_ms = {k: v[1] for k, v in stats.items()}
     total_kernel_ms = sum(kernel_ms.values())
+    upd = update_roofline(w, prec == S.SACD_BF16_GATHER, kernel_ms, args.steps, peak)
     g.close()
 
     if args.kernels_only:  # short run for a profiler: device-resident steps only
@@ -355,6 +356,7 @@ def ours_arm(args):
                 "bytes_model": "COO model: nnz*(4 + 4N + (N-1)*R*s) + I_n*R*4 per launch",
                 "mttkrp_share": mt_ms / total_kernel_ms if total_kernel_ms else None,
             },
+            "update_roofline": upd,
             "kernel_ms_per_step": {k: v / args.steps for k, v in kernel_ms.items()},
             "gpu_launches": int(launches),
             "e2e": {
@@ -373,6 +375,33 @@ def ours_arm(args):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+# FP32 instruction peak of one GB300: 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock),
+# one FP32 operation (an FMA counts as one) per lane and clock.
+FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+
+
+def update_roofline(w, bf16, kernel_ms, steps, hbm_peak):
+    """Select/update roofline of pass 1 + pass 2 (one element = one factor entry of a mode step):
+    algorithmic bytes 20 per element (read M, A, z^{k-1}; write A, z^{k-1}; 22 with the BF16
+    mirror) against the HBM copy peak, and, for pass 1, which is bound by its compensated
+    products, 10 FP32 operations per product (exact product: 2, TwoSum: 6, error terms: 2) times R
+    products per element against the FP32 instruction peak."""
+    elems = sum(w.dims) * w.rank * steps
+    bpe = 20 + (2 if bf16 else 0)
+    t = (kernel_ms.get("pass1_grad_importance", 0.0) + kernel_ms.get("pass2_select_update", 0.0)) / 1e3
+    t1 = kernel_ms.get("pass1_grad_importance", 0.0) / 1e3
+    if t <= 0 or t1 <= 0:
+        return None
+    gbs = elems * bpe / t / 1e9
+    tops = elems * w.rank * 10 / t1 / 1e12
+    return {"kernels": ["pass1_grad_importance", "pass2_select_update"], "bytes_per_element": bpe,
+            "elements_per_step": elems // steps, "achieved_gbs": gbs, "hbm_peak_gbs": hbm_peak,
+            "frac_hbm": gbs / hbm_peak,
+            "pass1": {"bound": "alu", "ops_per_element": 10 * w.rank, "achieved_tops": tops,
+                      "peak_tops": FP32_PEAK_TOPS, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
+                      "frac": tops / FP32_PEAK_TOPS}}
 
 
 def _gen_job(w):

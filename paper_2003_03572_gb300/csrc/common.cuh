@@ -50,6 +50,8 @@ struct StepDesc {
   const int4* fix_chunks;   // {row, first tile, first partial, count} chunks of heavy rows
   int64_t nfix_chunks;
   float* carry2;            // nfix_chunks x Rp chunk sums
+  const int32_t* rowfix;    // I: -1, or i >= 0 (split_light[i]), or -2 - j (split_heavy[j]);
+                            // pass 1 finishes these rows of M when the fix-up was folded into it
   // ---- update of factor n
   float* A;              // I x Rp FP32 master
   __nv_bfloat16* A16;    // I x Rp BF16 mirror (or null)

@@ -15,6 +15,7 @@ void set_last_error(const char* msg);
 // ---- MTTKRP (mttkrp.cu)
 void launch_mttkrp(const StepDesc* d_descs, const int64_t* d_tile_base, int njobs, int64_t total_tiles, int prec,
                    int rv, int nother, cudaStream_t st);
+void launch_rowfix(const int4* light, int64_t nl, const int4* heavy, int64_t nh, int32_t* rowfix, cudaStream_t st);
 void launch_fixup_light(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st);
 void launch_fixup_chunks(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st);
 constexpr int kFixChunk = 128;  // partials per level-1 chunk of a heavy split row

@@ -587,6 +587,19 @@ void launch_mttkrp(const StepDesc* d_descs, const int64_t* d_tile_base, int njob
     launch_mttkrp_prec<1>(d_descs, d_tile_base, njobs, total_tiles, rv, nother, st);
 }
 
+// row -> split entry map (-1 elsewhere; the caller fills it with -1 first)
+__global__ void rowfix_kernel(const int4* __restrict__ light, int64_t nl, const int4* __restrict__ heavy, int64_t nh,
+                              int32_t* __restrict__ rowfix) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nl) rowfix[light[i].x] = (int32_t)i;
+  else if (i < nl + nh) rowfix[heavy[i - nl].x] = (int32_t)(-2 - (i - nl));
+}
+
+void launch_rowfix(const int4* light, int64_t nl, const int4* heavy, int64_t nh, int32_t* rowfix, cudaStream_t st) {
+  if (nl + nh <= 0) return;
+  rowfix_kernel<<<(unsigned)((nl + nh + 255) / 256), 256, 0, st>>>(light, nl, heavy, nh, rowfix);
+}
+
 void launch_fixup_light(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st) {
   if (total <= 0) return;
   const int64_t blocks = (total * 32 + 255) / 256;

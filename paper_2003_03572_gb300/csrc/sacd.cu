@@ -47,6 +47,7 @@ struct ModeData {
   int64_t nheavy = 0;
   int4* chunks = nullptr;
   int64_t nchunks = 0;
+  int32_t* rowfix = nullptr;     // I: row -> split entry (see StepDesc::rowfix)
   int4* split_tmp = nullptr;     // create-time list of split rows (ntiles entries)
   uint32_t* split_pos = nullptr;
   uint32_t* split_tot = nullptr;
@@ -233,7 +234,10 @@ struct KScope {
   ~KScope() { prof_record(c, cls, false); }
 };
 
-void enqueue_mttkrp(sacd_ctx* c, int n) {
+// With `fold`, pass 1 of the same mode step finishes the rows split across tiles (light rows and
+// the chunk sums of heavy rows, StepDesc::rowfix) and writes them into M, so only the chunk
+// level runs here; without it (M needed on its own, e.g. for the objective) every level runs.
+void enqueue_mttkrp(sacd_ctx* c, int n, bool fold) {
   ModeData& md = c->m[n];
   StepDesc* dd = c->ddesc + n;
   if (c->nnz == 0) {
@@ -244,14 +248,14 @@ void enqueue_mttkrp(sacd_ctx* c, int n) {
     KScope k(c, K_MTTKRP);
     launch_mttkrp(dd, c->zero64, 1, md.ntiles, c->prec, c->rv, c->N - 1, c->st);
   }
-  if (md.nlight) {
+  if (md.nlight && !fold) {
     KScope k(c, K_FIXUP);
     launch_fixup_light(dd, c->zero64, 1, md.nlight, c->st);
   }
   if (md.nheavy) {
     KScope k(c, K_FIXUP);
     launch_fixup_chunks(dd, c->zero64, 1, md.nchunks, c->st);
-    launch_fixup_heavy(dd, c->zero64, 1, md.nheavy, c->st);
+    if (!fold) launch_fixup_heavy(dd, c->zero64, 1, md.nheavy, c->st);
   }
 }
 
@@ -268,7 +272,7 @@ void enqueue_step(sacd_ctx* c, int n) {
     KScope k(c, K_HL);
     launch_hl(dd, 1, c->st);
   }
-  enqueue_mttkrp(c, n);
+  enqueue_mttkrp(c, n, true);
   {
     KScope k(c, K_PASS1);
     launch_pass1(dd, c->zero64, 1, md.p1_blocks, pass_smem_bytes(c->Rp), c->st);
@@ -294,7 +298,7 @@ void enqueue_iteration_dag(sacd_ctx* c) {
   for (int n = 0; n < N; ++n) {
     ModeData& md = c->m[n];
     StepDesc* dd = c->ddesc + n;
-    enqueue_mttkrp(c, n);
+    enqueue_mttkrp(c, n, true);
     cudaStreamWaitEvent(c->st, ev[1 + n], 0);
     launch_pass1(dd, c->zero64, 1, md.p1_blocks, pass_smem_bytes(c->Rp), c->st);
     launch_pass2(dd, c->zero64, 1, md.p2_blocks, pass_smem_bytes(c->Rp), c->st);
@@ -526,6 +530,10 @@ sacd_status finish_split_lists(sacd_ctx* c) {
       CK(cudaMemcpyAsync(md.split_light, light.data(), sizeof(int4) * light.size(), cudaMemcpyHostToDevice, c->st));
     if (!heavy.empty())
       CK(cudaMemcpyAsync(md.split_heavy, heavy.data(), sizeof(int4) * heavy.size(), cudaMemcpyHostToDevice, c->st));
+    if (!md.rowfix) TRY(dalloc(c, &md.rowfix, std::max<int64_t>(md.I, 1)));
+    CK(cudaMemsetAsync(md.rowfix, 0xff, sizeof(int32_t) * std::max<int64_t>(md.I, 1), c->st));
+    launch_rowfix(md.split_light, md.nlight, md.split_heavy, md.nheavy, md.rowfix, c->st);
+    CK(cudaGetLastError());
   }
   return SACD_OK;
 }
@@ -792,6 +800,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     d.fix_chunks = md.chunks;
     d.nfix_chunks = md.nchunks;
     d.carry2 = c->carry2;
+    d.rowfix = md.rowfix;
     d.A = md.A;
     d.A16 = md.A16;
     d.G = c->G;
@@ -924,7 +933,7 @@ sacd_status sacd_iterate(sacd_ctx* c, int32_t iters) {
 sacd_status sacd_fit(sacd_ctx* c, double* objective, double* fit) {
   TRY(check_ctx(c));
   if (!c->mlast_valid) {
-    enqueue_mttkrp(c, c->N - 1);
+    enqueue_mttkrp(c, c->N - 1, false);
     c->mlast_valid = true;
   }
   {
@@ -1239,6 +1248,7 @@ sacd_status sacd_set_tiling(sacd_ctx* c, int32_t mode, int32_t sub) {
     d.nsplit_heavy = md.nheavy;
     d.fix_chunks = md.chunks;
     d.nfix_chunks = md.nchunks;
+    d.rowfix = md.rowfix;
     return upload_descs(c);
   } catch (const std::bad_alloc&) {
     return fail(SACD_ENOMEM, "host allocation failed");
@@ -1500,9 +1510,7 @@ struct BatchPlan {
         cudaMemsetAsync(c->m[n].M, 0, (size_t)c->m[n].I * c->Rp * sizeof(float), st);
       for (const PlanClass& pc : pm.classes)
         launch_mttkrp(pc.d_descs, pc.d_tile_base, pc.njobs, pc.tiles, pc.prec, pc.rv, pc.nother, st);
-      launch_fixup_light(pm.d_descs, pm.d_light, pm.njobs, pm.light, st);
-      launch_fixup_chunks(pm.d_descs, pm.d_chunk, pm.njobs, pm.chunk, st);
-      launch_fixup_heavy(pm.d_descs, pm.d_heavy, pm.njobs, pm.heavy, st);
+      launch_fixup_chunks(pm.d_descs, pm.d_chunk, pm.njobs, pm.chunk, st);  // the rest is folded into pass 1
       launch_pass1(pm.d_descs, pm.d_p1, pm.njobs, pm.p1, pm.smem, st);
       launch_pass2(pm.d_descs, pm.d_p2, pm.njobs, pm.p2, pm.smem, st);
       for (const PlanClass& pc : pm.classes)
@@ -1610,7 +1618,7 @@ sacd_status sacd_batch_fit(sacd_batch* b, double* objective, double* fit) {
   if (b->poisoned) return fail(SACD_ESTATE, "batch is poisoned by an earlier CUDA error");
   for (sacd_ctx* c : b->jobs)
     if (!c->mlast_valid) {
-      enqueue_mttkrp(c, c->N - 1);
+      enqueue_mttkrp(c, c->N - 1, false);
       c->mlast_valid = true;
     }
   b->plan.enqueue_fit(b->st);
@@ -1690,7 +1698,8 @@ int64_t estimate_bytes(const sacd_config* c) {
     Imax = std::max<int64_t>(Imax, c->dims[n]);
   }
   const int64_t csf = N * nnz * 4 * (N + 1);
-  const int64_t facs = rows * Rp * (12 + (c->precision == SACD_BF16_GATHER ? 2 : 0)) + N * (int64_t)Rp * Rp * 8;
+  const int64_t facs = rows * Rp * (12 + (c->precision == SACD_BF16_GATHER ? 2 : 0)) + N * (int64_t)Rp * Rp * 8 +
+                       rows * 4;  // + the row -> split entry maps
   const int64_t tiles = nnz / 32 + 1;
   const int64_t gram_blocks = std::min<int64_t>((Imax + 4096 / Rp - 1) / (4096 / Rp), 4 * 152);
   const int64_t scratch = Imax * Rp * 6 + tiles * (2 * Rp * 4 + 16) + gram_blocks * Rp * Rp * 8 + (1 << 20);

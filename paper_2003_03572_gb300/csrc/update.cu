@@ -137,6 +137,40 @@ __device__ __forceinline__ void dot2_acc(float a, float b, float& hi, float& lo)
 }
 
 // ------------------------------------------------------------------------------------------
+// A row of M split across MTTKRP tiles, finished from the partials (columns c0 .. c0+7): a light
+// row sums slot 1 of its first tile and slot 0 of the following tiles in tile order (the order of
+// the separate light fix-up), a heavy row its chunk sums in chunk order.
+__device__ __forceinline__ void split_row_sum(const StepDesc* __restrict__ dp, int32_t fx, int c0, float4& m0,
+                                              float4& m1) {
+  const int nvec = dp->Rp >> 2, v0 = c0 >> 2;
+  const float4* __restrict__ src;
+  int64_t first, count, stride;
+  if (fx >= 0) {
+    const int4 s = dp->split_light[fx];  // {row, first tile, last tile, 0}
+    src = reinterpret_cast<const float4*>(dp->carry);
+    m0 = src[((int64_t)s.y * 2 + 1) * nvec + v0];
+    m1 = src[((int64_t)s.y * 2 + 1) * nvec + v0 + 1];
+    first = (int64_t)s.y * 2 + 2;  // slot 0 of tile s.y + 1
+    count = (int64_t)s.z - s.y;
+    stride = 2 * (int64_t)nvec;
+  } else {
+    const int4 s = dp->split_heavy[-2 - fx];  // {row, first chunk, chunk count, 0}
+    src = reinterpret_cast<const float4*>(dp->carry2);
+    m0 = src[(int64_t)s.y * nvec + v0];
+    m1 = src[(int64_t)s.y * nvec + v0 + 1];
+    first = (int64_t)s.y + 1;
+    count = (int64_t)s.z - 1;
+    stride = nvec;
+  }
+  for (int64_t k = 0; k < count; ++k) {
+    const int64_t o = first * nvec + k * stride;
+    const float4 a = src[o + v0], b = src[o + v0 + 1];
+    m0.x += a.x; m0.y += a.y; m0.z += a.z; m0.w += a.w;
+    m1.x += b.x; m1.y += b.y; m1.z += b.z; m1.w += b.w;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // pass 1: G = A H - M with compensated dot products (rounded once to FP32), z, ti
 __global__ void __launch_bounds__(256) pass1_kernel(const StepDesc* __restrict__ descs,
                                                    const int64_t* __restrict__ base, int njobs) {
@@ -151,7 +185,8 @@ __global__ void __launch_bounds__(256) pass1_kernel(const StepDesc* __restrict__
   const int R = dp->R, Rp = dp->Rp, ST = Rp + 1;
   const int64_t I = dp->I;
   const float* __restrict__ A = dp->A;
-  const float* __restrict__ M = dp->M;
+  float* __restrict__ M = dp->M;
+  const int32_t* __restrict__ rowfix = dp->rowfix;
   float* __restrict__ G = dp->G;
   const float* __restrict__ invh = dp->invh;
   const float* __restrict__ lh = dp->lh;
@@ -170,10 +205,23 @@ __global__ void __launch_bounds__(256) pass1_kernel(const StepDesc* __restrict__
   __syncthreads();
   const int rl = threadIdx.x / TPR, c0 = (threadIdx.x % TPR) * 8;
   float zsum = 0.f;
+  float4 m0 = make_float4(0.f, 0.f, 0.f, 0.f), m1 = m0;
+  if (rl < nrows) {
+    // M of the row; rows split across MTTKRP tiles are finished here and written back
+    const int64_t row = row0 + rl;
+    float4* m4 = reinterpret_cast<float4*>(M + row * Rp + c0);
+    const int32_t fx = rowfix ? __ldg(rowfix + row) : -1;
+    if (fx != -1) {
+      split_row_sum(dp, fx, c0, m0, m1);
+      m4[0] = m0;
+      m4[1] = m1;
+    } else if (c0 < R) {
+      m0 = m4[0];
+      m1 = m4[1];
+    }
+  }
   if (rl < nrows && c0 < R) {
     const int64_t row = row0 + rl;
-    const float4* m4 = reinterpret_cast<const float4*>(M + row * Rp + c0);
-    const float4 m0 = m4[0], m1 = m4[1];
     float hi[8] = {-m0.x, -m0.y, -m0.z, -m0.w, -m1.x, -m1.y, -m1.z, -m1.w};
     float lo[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const float* arow = As + rl * ST;

@@ -59,3 +59,21 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["unit"] == "mode-steps/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_update_roofline_arithmetic():
+    """Select/update roofline: 20 B per element (22 with the BF16 mirror) over pass 1 + pass 2,
+    and 10 R FP32 operations per element over pass 1, against the stated peaks."""
+    from paper_2003_03572_gb300 import synth
+
+    w = synth.WORKLOADS["zipf1.1-50000x20000x500-5M-r32"]
+    E = sum(w.dims) * w.rank
+    km = {"pass1_grad_importance": 2.0, "pass2_select_update": 3.0}  # ms over 4 steps
+    r = bench.update_roofline(w, False, km, 4, 6765.7)
+    assert r["elements_per_step"] == E
+    assert r["achieved_gbs"] == pytest.approx(4 * E * 20 / 5e-3 / 1e9)
+    assert r["frac_hbm"] == pytest.approx(r["achieved_gbs"] / 6765.7)
+    assert r["pass1"]["achieved_tops"] == pytest.approx(4 * E * 32 * 10 / 2e-3 / 1e12)
+    assert r["pass1"]["peak_tops"] == pytest.approx(152 * 128 * 2.07e9 / 1e12)
+    assert bench.update_roofline(w, True, km, 4, 6765.7)["bytes_per_element"] == 22
+    assert bench.update_roofline(w, False, {}, 4, 6765.7) is None
