@@ -223,7 +223,9 @@ def ours_arm(args):
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
     w = synth.WORKLOADS[args.workload]
-    idx, vals, init = synth.make_workload(w)
+    if args.scale != 1.0 and not args.kernels_only:
+        raise SystemExit("--scale is for --kernels-only profiling runs")
+    idx, vals, init = synth.make_workload(w, scale=args.scale)
     N = w.nmodes
     prec = S.SACD_BF16_GATHER if w.precision == "bf16" else S.SACD_FP32
     stream = torch.cuda.Stream(device=dev)
@@ -277,7 +279,7 @@ def ours_arm(args):
 
     if args.kernels_only:  # short run for a profiler: device-resident steps only
         if rank == 0:
-            print(json.dumps({"kernels_only": True, "value": value, "unit": "mode-steps/s",
+            print(json.dumps({"kernels_only": True, "scale": args.scale, "value": value, "unit": "mode-steps/s",
                               "kernel_ms_per_step": {k: v / args.steps for k, v in kernel_ms.items()}}))
         return 0
 
@@ -569,6 +571,9 @@ def main():
     ap.add_argument("--e2e-reps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true", help="skip the end-to-end and CPU legs (profiling)")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="with --kernels-only: keep this fraction of the workload's nonzeros (same dims and rank), "
+                         "for profiler captures of a smaller case")
     ap.add_argument("--cpu-baseline-child", action="store_true")
     ap.add_argument("--batched", action="store_true", help="the many-small-jobs workload (batched vs one at a time)")
     ap.add_argument("--jobs", type=int, default=512)

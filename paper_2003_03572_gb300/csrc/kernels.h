@@ -37,6 +37,7 @@ void launch_gram(const StepDesc* d_descs, const int64_t* d_base, int njobs, int6
 int gram_reduce_blocks(int Rp);
 void launch_gram_reduce(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks,
                         cudaStream_t st);
+int64_t fit_blocks_for(int64_t I, int Rp);
 void launch_fit(const FitDesc* d_fit, const int64_t* d_base, int njobs, int64_t total_blocks, cudaStream_t st);
 void launch_to_bf16(const float* src, void* dst, int64_t n, cudaStream_t st);
 void launch_rmse(const int32_t* idx, const float* vals, int64_t n, const float* const* fac, int N, int R, int Rp,

@@ -116,6 +116,7 @@ struct sacd_ctx {
   FitDesc* dfit = nullptr;
   double* fitpart = nullptr;
   double* fitout = nullptr;
+  double* fit_host = nullptr;  // pinned, 4 doubles: the objective read back by sacd_fit
   int64_t* fitbase = nullptr;  // {0, fit_blocks}
   int64_t fit_blocks = 0;
   cudaGraph_t graph = nullptr;
@@ -830,7 +831,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
   // ---- fit descriptor
   {
     const int L = N - 1;
-    c->fit_blocks = std::max<int64_t>(1, (c->m[L].I + 255) / 256);
+    c->fit_blocks = fit_blocks_for(c->m[L].I, c->Rp);
     TRY(dalloc(c, &c->fitpart, c->fit_blocks));
     TRY(dalloc(c, &c->fitout, 4));
     TRY(dalloc(c, &c->dfit, 1));
@@ -940,11 +941,15 @@ sacd_status sacd_fit(sacd_ctx* c, double* objective, double* fit) {
     KScope k(c, K_FIT);
     launch_fit(c->dfit, c->fitbase, 1, c->fit_blocks, c->st);
   }
-  double out[4];
-  CK(cudaMemcpyAsync(out, c->fitout, sizeof(out), cudaMemcpyDeviceToHost, c->st));
+  if (!c->fit_host) {
+    void* h = nullptr;
+    CK(cudaMallocHost(&h, 4 * sizeof(double)));
+    c->fit_host = static_cast<double*>(h);
+  }
+  CK(cudaMemcpyAsync(c->fit_host, c->fitout, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  if (objective) *objective = out[0];
-  if (fit) *fit = out[1];
+  if (objective) *objective = c->fit_host[0];
+  if (fit) *fit = c->fit_host[1];
   return SACD_OK;
 }
 
@@ -1340,6 +1345,7 @@ void sacd_destroy(sacd_ctx* c) {
     if (e) cudaEventDestroy(e);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+  if (c->fit_host) cudaFreeHost(c->fit_host);
   cudaGetLastError();
   delete c;
 }

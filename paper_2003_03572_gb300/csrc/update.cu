@@ -10,6 +10,8 @@
 // GB300 runs FP64 at a small fraction of its FP32 rate, so the sums that decide accuracy
 // (A H - M under cancellation, the Gauss-Seidel gradient, the Grams) use error-free FP32
 // transformations (exact products and sums carried as (hi, lo) pairs) instead of FP64 FMAs.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -418,33 +420,25 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) ahi[u] = alo[u] = 0.f;
-    for (int w0 = 0; w0 < TPR; w0 += 4) {  // 32 columns per word, in order
-      uint32_t rowbits = 0;
-      if (live)
-        for (int k = 0; k < 4 && w0 + k < TPR; ++k) rowbits |= (uint32_t)rsel[w0 + k] << (8 * k);
-      uint32_t wbits = __reduce_or_sync(0xffffffffu, rowbits);
-      while (wbits) {
-        const int b = __ffs(wbits) - 1;
-        wbits &= wbits - 1u;
-        const int r = w0 * 8 + b, ur = r & 7;
-        // the owner lane's current gradient of column r, broadcast to its row's lanes
-        float g0 = gv[0], gl0 = glv[0], h0 = ahi[0], l0 = alo[0];
+    // 8-column blocks in order; lane o of a row owns block o, and within a block the column's
+    // register index u is static, so each lane forms its candidate gradient directly and the
+    // owner's value reaches the row by one shuffle
+    for (int o = 0; o < TPR; ++o) {
+      const uint32_t rowbyte = live ? (uint32_t)rsel[o] : 0u;
+      const uint32_t wb = __reduce_or_sync(0xffffffffu, rowbyte);
+      if (wb == 0u) continue;
 #pragma unroll
-        for (int u = 1; u < 8; ++u)
-          if (ur == u) {
-            g0 = gv[u];
-            gl0 = glv[u];
-            h0 = ahi[u];
-            l0 = alo[u];
-          }
+      for (int u = 0; u < 8; ++u) {
+        if (!((wb >> u) & 1u)) continue;
+        const int r = 8 * o + u;
         float s2, t2;
-        two_sum(g0, h0, s2, t2);
-        const float gown = __fadd_rn(s2, __fadd_rn(__fadd_rn(t2, l0), gl0));
-        const float g = __shfl_sync(0xffffffffu, gown, r >> 3, TPR);
+        two_sum(gv[u], ahi[u], s2, t2);
+        const float gown = __fadd_rn(s2, __fadd_rn(__fadd_rn(t2, alo[u]), glv[u]));
+        const float g = __shfl_sync(0xffffffffu, gown, o, TPR);
         const float ar = arow[r];
-        const float s = ((rowbits >> b) & 1u) ? sacd_step(ar, g, ihs[r]) : 0.f;
+        const float s = ((rowbyte >> u) & 1u) ? sacd_step(ar, g, ihs[r]) : 0.f;
         if (s != 0.f) {
-          if ((r >> 3) == ch) {
+          if (o == ch) {
             arow[r] = __fadd_rn(ar, s);
             dirty = true;
           }
@@ -607,20 +601,17 @@ __global__ void __launch_bounds__(256) fit_kernel(const FitDesc* __restrict__ fd
   const int64_t nblk = base[jb + 1] - base[jb];
   __shared__ double red[256];
   __shared__ int amlast;
-  const int64_t i = lb * blockDim.x + threadIdx.x;
+  // <X, model> = sum of A .* M over the last mode (Eq. 8 contracted with the MTTKRP), as 16-byte
+  // vectors over all I x Rp entries (the padding columns of A are zero). A product of two FP32
+  // values is exact in FP64, so the FP64 sum of the exact products is accurate.
   double part = 0.0;
-  if (i < f.I) {
-    float hi = 0.f, lo = 0.f;
-    const float* a = f.A + i * f.Rp;
-    const float* m = f.M + i * f.Rp;
-    for (int r = 0; r < f.R; ++r) {
-      float p, e, s, t;
-      two_prod(a[r], m[r], p, e);
-      two_sum(hi, p, s, t);
-      hi = s;
-      lo = __fadd_rn(lo, __fadd_rn(t, e));
-    }
-    part = (double)hi + (double)lo;
+  const int64_t nv = f.I * f.Rp / 4;
+  const float4* __restrict__ a4 = reinterpret_cast<const float4*>(f.A);
+  const float4* __restrict__ m4 = reinterpret_cast<const float4*>(f.M);
+  for (int64_t v = lb * blockDim.x + threadIdx.x; v < nv; v += nblk * blockDim.x) {
+    const float4 a = a4[v], m = m4[v];
+    part += (double)a.x * (double)m.x + (double)a.y * (double)m.y + (double)a.z * (double)m.z +
+            (double)a.w * (double)m.w;
   }
   const double bs = block_sum(part, red);
   if (threadIdx.x == 0) {
@@ -654,7 +645,12 @@ __global__ void __launch_bounds__(256) fit_kernel(const FitDesc* __restrict__ fd
   }
 }
 
-// base[0..njobs]: prefix of the jobs' block counts (ceil(I / 256) of their last mode)
+// base[0..njobs]: prefix of the jobs' block counts (fit_blocks_for of their last mode)
+int64_t fit_blocks_for(int64_t I, int Rp) {
+  const int64_t vecs = I * Rp / 4;
+  return std::max<int64_t>(1, std::min<int64_t>((vecs + 1023) / 1024, 152 * 4));  // ~4 vectors per thread
+}
+
 void launch_fit(const FitDesc* d_fit, const int64_t* d_base, int njobs, int64_t total_blocks, cudaStream_t st) {
   fit_kernel<<<(unsigned)(total_blocks > 0 ? total_blocks : 1), 256, 0, st>>>(d_fit, d_base, njobs);
 }
