@@ -66,6 +66,35 @@ constexpr int kWarpsPerBlock = SACD_MTTKRP_WARPS;
 #define SACD_MTTKRP_STAGE_NNZ 0
 #endif
 
+// Packed two-lane FP32 arithmetic (sm_100 family): each lane is an IEEE round-to-nearest
+// multiply or add, so the results equal the scalar operations element by element, at half the
+// instruction count.
+#ifndef SACD_MTTKRP_F32X2
+#define SACD_MTTKRP_F32X2 1
+#endif
+__device__ __forceinline__ void mul2_inplace(float& a0, float& a1, float b0, float b1) {
+#if !SACD_MTTKRP_F32X2
+  a0 = __fmul_rn(a0, b0);
+  a1 = __fmul_rn(a1, b1);
+  return;
+#endif
+  asm("{\n\t.reg .b64 ra, rb;\n\tmov.b64 ra, {%0, %1};\n\tmov.b64 rb, {%2, %3};\n\t"
+      "mul.rn.f32x2 ra, ra, rb;\n\tmov.b64 {%0, %1}, ra;\n\t}"
+      : "+f"(a0), "+f"(a1)
+      : "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void add2_inplace(float& a0, float& a1, float b0, float b1) {
+#if !SACD_MTTKRP_F32X2
+  a0 = __fadd_rn(a0, b0);
+  a1 = __fadd_rn(a1, b1);
+  return;
+#endif
+  asm("{\n\t.reg .b64 ra, rb;\n\tmov.b64 ra, {%0, %1};\n\tmov.b64 rb, {%2, %3};\n\t"
+      "add.rn.f32x2 ra, ra, rb;\n\tmov.b64 {%0, %1}, ra;\n\t}"
+      : "+f"(a0), "+f"(a1)
+      : "f"(b0), "f"(b1));
+}
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
@@ -221,7 +250,8 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
               float v[S::W];
               GatherVec<PREC>::load(fac[m], (int64_t)ix[m][u] * RV + lig + k * S::LPR, v);
 #pragma unroll
-              for (int i = 0; i < S::W; ++i) prod[u][k * S::W + i] *= v[i];
+              for (int i = 0; i < S::W; i += 2)
+                mul2_inplace(prod[u][k * S::W + i], prod[u][k * S::W + i + 1], v[i], v[i + 1]);
             }
           }
         }
@@ -242,7 +272,7 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
           for (int i = 0; i < S::NV; ++i) acc[i] = 0.f;
         }
 #pragma unroll
-        for (int i = 0; i < S::NV; ++i) acc[i] += prod[u][i];
+        for (int i = 0; i < S::NV; i += 2) add2_inplace(acc[i], acc[i + 1], prod[u][i], prod[u][i + 1]);
       }
     }
   };
@@ -297,6 +327,16 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
           for (int m = 0; m < MAXO; ++m) {
             const int4 c4 = *reinterpret_cast<const int4*>(sb + ((2 + m) * S::G + g) * C + o);
             ix[m][0] = c4.x; ix[m][1] = c4.y; ix[m][2] = c4.z; ix[m][3] = c4.w;
+          }
+        } else if constexpr (kUnroll == 2) {
+          const int2 r2 = *reinterpret_cast<const int2*>(sb + (0 * S::G + g) * C + o);
+          const int2 x2 = *reinterpret_cast<const int2*>(sb + (1 * S::G + g) * C + o);
+          rows[0] = r2.x; rows[1] = r2.y;
+          xs[0] = __int_as_float(x2.x); xs[1] = __int_as_float(x2.y);
+#pragma unroll
+          for (int m = 0; m < MAXO; ++m) {
+            const int2 c2 = *reinterpret_cast<const int2*>(sb + ((2 + m) * S::G + g) * C + o);
+            ix[m][0] = c2.x; ix[m][1] = c2.y;
           }
         } else {
 #pragma unroll
