@@ -118,6 +118,58 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
 }
 
+// Packed FP32 pairs (sm_100 family): one 64-bit register holds two floats (the first in the low
+// half, as in memory). Every lane of these operations is an IEEE round-to-nearest add, subtract,
+// multiply or fused multiply-add, identical to the scalar operation, at half the instructions.
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p f2_pack(float a, float b) {
+  f2p r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float f2_x(f2p v) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  return a;
+}
+__device__ __forceinline__ float f2_y(f2p v) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  return b;
+}
+__device__ __forceinline__ f2p f2_add(f2p a, f2p b) {
+  f2p r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2p f2_sub(f2p a, f2p b) {
+  f2p r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2p f2_mul(f2p a, f2p b) {
+  f2p r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2p f2_fma(f2p a, f2p b, f2p c) {
+  f2p r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// Compensated accumulation of a * b into (hi, lo), two lanes at once: p = a b rounded,
+// -e = RN(p - a b) exactly (na = -a), TwoSum of hi and p, lo += t + e (as t - (-e), the same
+// rounding). Lane for lane the same result as the scalar two_prod / two_sum sequence.
+__device__ __forceinline__ void dot2_acc2(f2p a, f2p na, f2p b, f2p& hi, f2p& lo) {
+  const f2p p = f2_mul(a, b);
+  const f2p ne = f2_fma(na, b, p);
+  const f2p s = f2_add(hi, p);
+  const f2p z = f2_sub(s, hi);
+  const f2p t = f2_add(f2_sub(hi, f2_sub(s, z)), f2_sub(p, z));
+  hi = s;
+  lo = f2_add(lo, f2_sub(t, ne));
+}
+
 // Map a global work item to (job, local item) with a prefix array base[0..njobs].
 __device__ __forceinline__ int find_job(const int64_t* base, int njobs, int64_t item) {
   int lo = 0, hi = njobs - 1;

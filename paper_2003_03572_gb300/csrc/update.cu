@@ -224,17 +224,27 @@ __global__ void __launch_bounds__(256) pass1_kernel(const StepDesc* __restrict__
   }
   if (rl < nrows && c0 < R) {
     const int64_t row = row0 + rl;
-    float hi[8] = {-m0.x, -m0.y, -m0.z, -m0.w, -m1.x, -m1.y, -m1.z, -m1.w};
-    float lo[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // column pairs (c0 + 2k, c0 + 2k + 1) in packed registers
+    f2p hi2[4] = {f2_pack(-m0.x, -m0.y), f2_pack(-m0.z, -m0.w), f2_pack(-m1.x, -m1.y), f2_pack(-m1.z, -m1.w)};
+    f2p lo2[4] = {0ull, 0ull, 0ull, 0ull};
     const float* arow = As + rl * ST;
     for (int j = 0; j < R; ++j) {
       const float aj = arow[j];
-      const float4 h0 = *reinterpret_cast<const float4*>(Hr + j * Rp + c0);
-      const float4 h1 = *reinterpret_cast<const float4*>(Hr + j * Rp + c0 + 4);
-      dot2_acc(aj, h0.x, hi[0], lo[0]); dot2_acc(aj, h0.y, hi[1], lo[1]);
-      dot2_acc(aj, h0.z, hi[2], lo[2]); dot2_acc(aj, h0.w, hi[3], lo[3]);
-      dot2_acc(aj, h1.x, hi[4], lo[4]); dot2_acc(aj, h1.y, hi[5], lo[5]);
-      dot2_acc(aj, h1.z, hi[6], lo[6]); dot2_acc(aj, h1.w, hi[7], lo[7]);
+      const f2p a2 = f2_pack(aj, aj), na2 = f2_pack(-aj, -aj);
+      const ulonglong2 h0 = *reinterpret_cast<const ulonglong2*>(Hr + j * Rp + c0);
+      const ulonglong2 h1 = *reinterpret_cast<const ulonglong2*>(Hr + j * Rp + c0 + 4);
+      dot2_acc2(a2, na2, h0.x, hi2[0], lo2[0]);
+      dot2_acc2(a2, na2, h0.y, hi2[1], lo2[1]);
+      dot2_acc2(a2, na2, h1.x, hi2[2], lo2[2]);
+      dot2_acc2(a2, na2, h1.y, hi2[3], lo2[3]);
+    }
+    float hi[8], lo[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      hi[2 * k] = f2_x(hi2[k]);
+      hi[2 * k + 1] = f2_y(hi2[k]);
+      lo[2 * k] = f2_x(lo2[k]);
+      lo[2 * k + 1] = f2_y(lo2[k]);
     }
     float g[8], gl[8];
 #pragma unroll
@@ -405,7 +415,8 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
     // exact start-of-step gradient plus an exactly accumulated correction, rounded once. The
     // warp walks the union of its rows' selected columns with uniform control flow (each row
     // applies only its own selections), so its rows never serialise on divergent paths.
-    float glv[8], ahi[8], alo[8];
+    float glv[8];
+    f2p ahi2[4], alo2[4];  // the pushed corrections of this lane's columns, as column pairs
     const float* __restrict__ Glo = dp->Glo;
     const uint8_t* rsel = selb + rl * TPR;
     const bool live = rl < nrows;
@@ -419,7 +430,7 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
       for (int u = 0; u < 8; ++u) glv[u] = 0.f;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) ahi[u] = alo[u] = 0.f;
+    for (int k = 0; k < 4; ++k) ahi2[k] = alo2[k] = 0ull;
     // 8-column blocks in order; lane o of a row owns block o, and within a block the column's
     // register index u is static, so each lane forms its candidate gradient directly and the
     // owner's value reaches the row by one shuffle
@@ -431,9 +442,11 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
       for (int u = 0; u < 8; ++u) {
         if (!((wb >> u) & 1u)) continue;
         const int r = 8 * o + u;
+        const float ah = (u & 1) ? f2_y(ahi2[u >> 1]) : f2_x(ahi2[u >> 1]);
+        const float al = (u & 1) ? f2_y(alo2[u >> 1]) : f2_x(alo2[u >> 1]);
         float s2, t2;
-        two_sum(gv[u], ahi[u], s2, t2);
-        const float gown = __fadd_rn(s2, __fadd_rn(__fadd_rn(t2, alo[u]), glv[u]));
+        two_sum(gv[u], ah, s2, t2);
+        const float gown = __fadd_rn(s2, __fadd_rn(__fadd_rn(t2, al), glv[u]));
         const float g = __shfl_sync(0xffffffffu, gown, o, TPR);
         const float ar = arow[r];
         const float s = ((rowbyte >> u) & 1u) ? sacd_step(ar, g, ihs[r]) : 0.f;
@@ -442,12 +455,13 @@ __global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__
             arow[r] = __fadd_rn(ar, s);
             dirty = true;
           }
-          const float4 hq0 = *reinterpret_cast<const float4*>(Hr + r * Rp + c0);
-          const float4 hq1 = *reinterpret_cast<const float4*>(Hr + r * Rp + c0 + 4);
-          dot2_acc(s, hq0.x, ahi[0], alo[0]); dot2_acc(s, hq0.y, ahi[1], alo[1]);
-          dot2_acc(s, hq0.z, ahi[2], alo[2]); dot2_acc(s, hq0.w, ahi[3], alo[3]);
-          dot2_acc(s, hq1.x, ahi[4], alo[4]); dot2_acc(s, hq1.y, ahi[5], alo[5]);
-          dot2_acc(s, hq1.z, ahi[6], alo[6]); dot2_acc(s, hq1.w, ahi[7], alo[7]);
+          const f2p s2p = f2_pack(s, s), ns2p = f2_pack(-s, -s);
+          const ulonglong2 hq0 = *reinterpret_cast<const ulonglong2*>(Hr + r * Rp + c0);
+          const ulonglong2 hq1 = *reinterpret_cast<const ulonglong2*>(Hr + r * Rp + c0 + 4);
+          dot2_acc2(s2p, ns2p, hq0.x, ahi2[0], alo2[0]);
+          dot2_acc2(s2p, ns2p, hq0.y, ahi2[1], alo2[1]);
+          dot2_acc2(s2p, ns2p, hq1.x, ahi2[2], alo2[2]);
+          dot2_acc2(s2p, ns2p, hq1.y, ahi2[3], alo2[3]);
         }
       }
     }
@@ -501,26 +515,54 @@ __device__ void gram_tile_pass(const StepDesc* __restrict__ dp, int64_t lb, int 
     for (int e = threadIdx.x; e < nr * Rp / 4; e += blockDim.x) dst[e] = src[e];
     __syncthreads();
     if (active) {
-      float hi[TS][TS], lo[TS][TS];
-#pragma unroll
-      for (int x = 0; x < TS; ++x)
-#pragma unroll
-        for (int y = 0; y < TS; ++y) hi[x][y] = lo[x][y] = 0.f;
-      for (int r = 0; r < nr; ++r) {
-        float ai[TS], aj[TS];
-#pragma unroll
-        for (int x = 0; x < TS; ++x) ai[x] = As[r * Rp + i0 + x];
-#pragma unroll
-        for (int y = 0; y < TS; ++y) aj[y] = As[r * Rp + j0 + y];
+      if constexpr (TS >= 2) {
+        // entries (x, y) and (x, y + 1) as packed pairs (j0 is even, so the pair loads align)
+        f2p hi2[TS][TS / 2], lo2[TS][TS / 2];
 #pragma unroll
         for (int x = 0; x < TS; ++x)
 #pragma unroll
-          for (int y = 0; y < TS; ++y) dot2_acc(ai[x], aj[y], hi[x][y], lo[x][y]);
+          for (int y = 0; y < TS / 2; ++y) hi2[x][y] = lo2[x][y] = 0ull;
+        for (int r = 0; r < nr; ++r) {
+          f2p aj2[TS / 2];
+#pragma unroll
+          for (int y = 0; y < TS / 2; ++y) aj2[y] = *reinterpret_cast<const f2p*>(As + r * Rp + j0 + 2 * y);
+#pragma unroll
+          for (int x = 0; x < TS; ++x) {
+            const float ai = As[r * Rp + i0 + x];
+            const f2p a2 = f2_pack(ai, ai), na2 = f2_pack(-ai, -ai);
+#pragma unroll
+            for (int y = 0; y < TS / 2; ++y) dot2_acc2(a2, na2, aj2[y], hi2[x][y], lo2[x][y]);
+          }
+        }
+#pragma unroll
+        for (int x = 0; x < TS; ++x)
+#pragma unroll
+          for (int y = 0; y < TS / 2; ++y) {
+            accd[x][2 * y] += (double)f2_x(hi2[x][y]) + (double)f2_x(lo2[x][y]);
+            accd[x][2 * y + 1] += (double)f2_y(hi2[x][y]) + (double)f2_y(lo2[x][y]);
+          }
+      } else {
+        float hi[TS][TS], lo[TS][TS];
+#pragma unroll
+        for (int x = 0; x < TS; ++x)
+#pragma unroll
+          for (int y = 0; y < TS; ++y) hi[x][y] = lo[x][y] = 0.f;
+        for (int r = 0; r < nr; ++r) {
+          float ai[TS], aj[TS];
+#pragma unroll
+          for (int x = 0; x < TS; ++x) ai[x] = As[r * Rp + i0 + x];
+#pragma unroll
+          for (int y = 0; y < TS; ++y) aj[y] = As[r * Rp + j0 + y];
+#pragma unroll
+          for (int x = 0; x < TS; ++x)
+#pragma unroll
+            for (int y = 0; y < TS; ++y) dot2_acc(ai[x], aj[y], hi[x][y], lo[x][y]);
+        }
+#pragma unroll
+        for (int x = 0; x < TS; ++x)
+#pragma unroll
+          for (int y = 0; y < TS; ++y) accd[x][y] += (double)hi[x][y] + (double)lo[x][y];
       }
-#pragma unroll
-      for (int x = 0; x < TS; ++x)
-#pragma unroll
-        for (int y = 0; y < TS; ++y) accd[x][y] += (double)hi[x][y] + (double)lo[x][y];
     }
     __syncthreads();
   }
