@@ -463,10 +463,10 @@ sacd_status build_mode(sacd_ctx* c, TmpAllocs& T, SortBufs& B, int n, const int3
     TRY(dalloc(c, &md.cidx, (size_t)(N - 1) * c->cstride));
     TRY(dalloc(c, &md.val, nnz));
   }
-  std::vector<int> order;
-  order.push_back(n);
-  for (int k = 0; k < N; ++k)
-    if (k != n) order.push_back(k);
+  // The distinct coordinates are in lexicographic (i_0, ..., i_{N-1}) order, so a stable sort by
+  // i_n alone yields (i_n, then the other modes in ascending mode order): the radix sort runs
+  // over the bits of I_n only, not over the whole coordinate tuple.
+  const std::vector<int> order{n};
   if (nnz > 0 && n > 0) {
     uint32_t* perm = nullptr;
     const int64_t cs = c->cstride;
@@ -727,12 +727,6 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     CK(cudaMemsetAsync(md.M, 0, sizeof(float) * I * Rp, c->st));
     if (cfg->init) {
       const cudaMemcpyKind k = cfg->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-      if (!cfg->inputs_on_device) {
-        for (int64_t e = 0; e < I * R; ++e) {
-          const float v = cfg->init[n][e];
-          if (!(v >= 0.f) || !std::isfinite(v)) return fail(SACD_EINVAL, "init values must be finite and >= 0");
-        }
-      }
       CK(cudaMemcpy2DAsync(md.A, sizeof(float) * Rp, cfg->init[n], sizeof(float) * R, sizeof(float) * R, I, k,
                            c->st));
     } else {
@@ -740,15 +734,13 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     }
     if (md.A16) launch_to_bf16(md.A, md.A16, I * Rp, c->st);
   }
-  if (cfg->init && cfg->inputs_on_device) {
-    unsigned int* bad;
-    TRY(T.get(&bad, 1));
-    CK(cudaMemsetAsync(bad, 0, sizeof(unsigned int), c->st));
-    for (int n = 0; n < N; ++n) launch_check_factor(c->m[n].A, c->m[n].I, R, Rp, bad, c->st);
-    unsigned int h_bad = 0;
-    CK(cudaMemcpyAsync(&h_bad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    if (h_bad) return fail(SACD_EINVAL, "init values must be finite and >= 0");
+  // initial factors from the caller are checked on the device (finite, >= 0); the flag is read
+  // at the synchronisation that ends context creation
+  unsigned int* init_bad = nullptr;
+  if (cfg->init) {
+    TRY(T.get(&init_bad, 1));
+    CK(cudaMemsetAsync(init_bad, 0, sizeof(unsigned int), c->st));
+    for (int n = 0; n < N; ++n) launch_check_factor(c->m[n].A, c->m[n].I, R, Rp, init_bad, c->st);
   }
   TRY(dalloc(c, &c->G, (size_t)Imax * Rp));
   TRY(dalloc(c, &c->Glo, (size_t)Imax * Rp));
@@ -859,6 +851,11 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
   for (int n = 0; n < N; ++n) enqueue_gram(c, n);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
+  if (init_bad) {
+    unsigned int h_bad = 0;
+    CK(cudaMemcpy(&h_bad, init_bad, sizeof(unsigned int), cudaMemcpyDeviceToHost));
+    if (h_bad) return fail(SACD_EINVAL, "init values must be finite and >= 0");
+  }
   guard.ok = true;
   *out = c;
   return SACD_OK;
