@@ -101,16 +101,16 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_from_profile(src_sha):
-    """DRAM bytes per MTTKRP launch from the committed ncu summary, if it was taken on the
-    current kernel source; else None."""
+def traffic_from_profile(src_sha, workload):
+    """DRAM bytes per MTTKRP launch of `workload` from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", "mttkrp_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("mttkrp_source_sha256") != src_sha:
         return None
-    return d.get("dram_bytes_per_launch")
+    return d.get("workloads", {}).get(workload, {}).get("dram_bytes_per_launch")
 
 
 def cpu_baseline_child(workload, nsteps):
@@ -271,7 +271,7 @@ def ours_arm(args):
     achieved = tot_bytes / (mt_ms / 1e3) / 1e9 if mt_ms > 0 else None
     peak, peak_kind = peaks()
     src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2003_03572_gb300", "csrc", "mttkrp.cu"), "rb").read()).hexdigest()
-    traffic = traffic_from_profile(src_sha)
+    traffic = traffic_from_profile(src_sha, w.name)
     kernel_ms = {k: v[1] for k, v in stats.items()}
     total_kernel_ms = sum(kernel_ms.values())
     upd = update_roofline(w, prec == S.SACD_BF16_GATHER, kernel_ms, args.steps, peak)

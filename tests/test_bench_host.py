@@ -77,3 +77,19 @@ def test_update_roofline_arithmetic():
     assert r["pass1"]["peak_tops"] == pytest.approx(152 * 128 * 2.07e9 / 1e12)
     assert bench.update_roofline(w, True, km, 4, 6765.7)["bytes_per_element"] == 22
     assert bench.update_roofline(w, False, {}, 4, 6765.7) is None
+
+
+def test_traffic_is_per_workload_and_per_kernel_source():
+    """The roofline's DRAM traffic comes from the committed ncu summary of the same workload, and
+    only while the MTTKRP source is the one that was captured."""
+    import hashlib
+
+    sha = hashlib.sha256(open(os.path.join(bench.ROOT, "paper_2003_03572_gb300", "csrc", "mttkrp.cu"), "rb").read())
+    sha = sha.hexdigest()
+    t5 = bench.traffic_from_profile(sha, "zipf1.1-50000x20000x500-5M-r32")
+    t50 = bench.traffic_from_profile(sha, "zipf1.2-200000x100000x10000x200-50M-r64-bf16")
+    if t5 is not None:  # captured on this source
+        assert 50e6 < t5 < 200e6  # ~ the compulsory stream of 5M sorted nonzeros (16 B each)
+        assert t50 is None or t50 > 10 * t5
+    assert bench.traffic_from_profile(sha, "no-such-workload") is None
+    assert bench.traffic_from_profile("0" * 64, "zipf1.1-50000x20000x500-5M-r32") is None
