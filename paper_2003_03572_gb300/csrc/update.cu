@@ -19,15 +19,22 @@ namespace sacd {
 
 // ------------------------------------------------------------------------------------------
 // block reductions with a fixed shape (deterministic)
+// (warp butterflies, then the warps' sums in warp order; `red` holds at least 33 entries)
 template <typename T>
 __device__ T block_sum(T v, T* red) {
-  red[threadIdx.x] = v;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
   __syncthreads();
-  for (int w = blockDim.x >> 1; w >= 1; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
+  if (w == 0) {
+    T r = l < (int)(blockDim.x >> 5) ? red[l] : T(0);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (l == 0) red[32] = r;
   }
-  T r = red[0];
+  __syncthreads();
+  const T r = red[32];
   __syncthreads();
   return r;
 }
@@ -164,7 +171,23 @@ __device__ __forceinline__ void split_row_sum(const StepDesc* __restrict__ dp, i
     count = (int64_t)s.z - 1;
     stride = nvec;
   }
-  for (int64_t k = 0; k < count; ++k) {
+  // four partials' loads in flight at a time, added in order
+  int64_t k = 0;
+  for (; k + 4 <= count; k += 4) {
+    float4 a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t o = first * nvec + (k + i) * stride;
+      a[i] = src[o + v0];
+      b[i] = src[o + v0 + 1];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      m0.x += a[i].x; m0.y += a[i].y; m0.z += a[i].z; m0.w += a[i].w;
+      m1.x += b[i].x; m1.y += b[i].y; m1.z += b[i].z; m1.w += b[i].w;
+    }
+  }
+  for (; k < count; ++k) {
     const int64_t o = first * nvec + k * stride;
     const float4 a = src[o + v0], b = src[o + v0 + 1];
     m0.x += a.x; m0.y += a.y; m0.z += a.z; m0.w += a.w;
@@ -174,7 +197,7 @@ __device__ __forceinline__ void split_row_sum(const StepDesc* __restrict__ dp, i
 
 // ------------------------------------------------------------------------------------------
 // pass 1: G = A H - M with compensated dot products (rounded once to FP32), z, ti
-__global__ void __launch_bounds__(256) pass1_kernel(const StepDesc* __restrict__ descs,
+__global__ void __launch_bounds__(256, 4) pass1_kernel(const StepDesc* __restrict__ descs,
                                                    const int64_t* __restrict__ base, int njobs) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
@@ -301,7 +324,7 @@ void launch_pass1(const StepDesc* d_descs, const int64_t* d_base, int njobs, int
 // pass 2: phase A (element-parallel): z from the stored gradient, selection, z^{k-1} <- z.
 // phase B (the lanes of a row that has a selected element): the selected columns in order,
 // s = max(0, u - g/h) - u (Eq. 12-13), with the gradient fix-up described below.
-__global__ void __launch_bounds__(256) pass2_kernel(const StepDesc* __restrict__ descs,
+__global__ void __launch_bounds__(256, 4) pass2_kernel(const StepDesc* __restrict__ descs,
                                                    const int64_t* __restrict__ base, int njobs) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
