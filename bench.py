@@ -82,7 +82,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons, pw = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -93,12 +93,17 @@ class ClockSampler:
                 mx = float(f[2])
             except ValueError:
                 continue
+            try:
+                pw.append(float(f[3]))
+            except ValueError:
+                pass
             for nm, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "sm_min_mhz": min(sm),
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def traffic_from_profile(src_sha, workload):
@@ -291,6 +296,8 @@ def ours_arm(args):
     h_out = [torch.empty(a.shape, dtype=torch.float32).pin_memory() for a in init]
     iters = w.iters
     e2e_times = []
+    clk2 = ClockSampler(local)
+    clk2.start()
     for rep in range(max(args.e2e_reps, 1) + 1):
         torch.cuda.synchronize(dev)
         barrier()
@@ -305,6 +312,7 @@ def ours_arm(args):
         t1 = time.perf_counter()
         if rep > 0:  # first solve is a warm-up (allocator, graph instantiation)
             e2e_times.append(t1 - t0)
+    e2e_clocks = clk2.stop()
     e2e_s = aggregate_over_ranks(statistics.median(e2e_times), ws, dev)
     e2e_value = replicas_value(N * iters, ws, e2e_s)
     h2d = int(len(vals) * (4 * N + 4) + sum(a.nbytes for a in init))
@@ -369,6 +377,8 @@ def ours_arm(args):
                 "step": f"one full solve from pinned host COO: create (copy + CSF build) + {iters} iterations "
                         f"+ fit + factors back",
                 "seconds_per_solve": e2e_s,
+                "solve_seconds": [round(t, 5) for t in e2e_times],
+                "clocks": e2e_clocks,
             },
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -568,7 +578,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--e2e-reps", type=int, default=3)
+    ap.add_argument("--e2e-reps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true", help="skip the end-to-end and CPU legs (profiling)")
     ap.add_argument("--scale", type=float, default=1.0,

@@ -131,6 +131,7 @@ sacd_status sacd_iterate(sacd_ctx* ctx, int32_t iters);
  * sacd_fit -- objective f = ||X - [[A]]||^2 over all cells (Eq. 6-8), as
  * ||X||^2 - 2<X, [[A]]> + sum_{r,s} prod_k (A_k^T A_k)_{rs}, in FP64, and
  * fit = 1 - sqrt(max(f, 0)) / ||X||. Waits for the stream. Either output pointer may be NULL.
+ * The first call allocates a 32-byte pinned host buffer for the read-back, owned by the context.
  */
 sacd_status sacd_fit(sacd_ctx* ctx, double* objective, double* fit);
 

@@ -87,8 +87,8 @@ struct FitDesc {
   int32_t R, Rp, N;
   const double* gram[SACD_MAXN];
   double norm_x_sq;
-  double* part;          // per-block partials of <X, model>
-  double* out;           // [0] objective [1] fit [2] <X, model> [3] ||model||^2
+  double* part;          // per-block partials: 2 x blocks (<X, model>, ||model||^2)
+  double* out;           // [0] objective [1] unused [2] <X, model> [3] ||model||^2
   unsigned int* counter;
 };
 

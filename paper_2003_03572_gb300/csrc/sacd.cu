@@ -331,6 +331,11 @@ sacd_status upload_descs(sacd_ctx* c) {
   return SACD_OK;
 }
 
+// fit = 1 - sqrt(max(f, 0)) / ||X|| (0 for an all-zero tensor)
+double fit_from_objective(double objective, double norm_x_sq) {
+  return norm_x_sq > 0 ? 1.0 - std::sqrt(std::max(objective, 0.0)) / std::sqrt(norm_x_sq) : 0.0;
+}
+
 sacd_status check_ctx(sacd_ctx* c) {
   if (!c) return fail(SACD_EINVAL, "null context");
   if (c->poisoned) return fail(SACD_ESTATE, "context is poisoned by an earlier CUDA error");
@@ -824,7 +829,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
   {
     const int L = N - 1;
     c->fit_blocks = fit_blocks_for(c->m[L].I, c->Rp);
-    TRY(dalloc(c, &c->fitpart, c->fit_blocks));
+    TRY(dalloc(c, &c->fitpart, 2 * c->fit_blocks));
     TRY(dalloc(c, &c->fitout, 4));
     TRY(dalloc(c, &c->dfit, 1));
     TRY(dalloc(c, &c->fitbase, 2));
@@ -946,7 +951,7 @@ sacd_status sacd_fit(sacd_ctx* c, double* objective, double* fit) {
   CK(cudaMemcpyAsync(c->fit_host, c->fitout, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   if (objective) *objective = c->fit_host[0];
-  if (fit) *fit = c->fit_host[1];
+  if (fit) *fit = fit_from_objective(c->fit_host[0], c->norm_x_sq);
   return SACD_OK;
 }
 
@@ -1635,7 +1640,7 @@ sacd_status sacd_batch_fit(sacd_batch* b, double* objective, double* fit) {
   }
   for (size_t j = 0; j < b->jobs.size(); ++j) {
     if (objective) objective[j] = out[4 * j];
-    if (fit) fit[j] = out[4 * j + 1];
+    if (fit) fit[j] = fit_from_objective(out[4 * j], b->jobs[j]->norm_x_sq);
   }
   return SACD_OK;
 }

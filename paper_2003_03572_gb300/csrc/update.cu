@@ -667,20 +667,33 @@ __global__ void __launch_bounds__(256) fit_kernel(const FitDesc* __restrict__ fd
   __shared__ double red[256];
   __shared__ int amlast;
   // <X, model> = sum of A .* M over the last mode (Eq. 8 contracted with the MTTKRP), as 16-byte
-  // vectors over all I x Rp entries (the padding columns of A are zero). A product of two FP32
-  // values is exact in FP64, so the FP64 sum of the exact products is accurate.
-  double part = 0.0;
+  // vectors over all I x Rp entries (the padding columns of A are zero): exact products and
+  // TwoSum on packed FP32 pairs, one conversion to FP64 per thread (this part runs FP64 at a
+  // small fraction of its FP32 rate).
   const int64_t nv = f.I * f.Rp / 4;
   const float4* __restrict__ a4 = reinterpret_cast<const float4*>(f.A);
   const float4* __restrict__ m4 = reinterpret_cast<const float4*>(f.M);
+  f2p hi0 = 0ull, lo0 = 0ull, hi1 = 0ull, lo1 = 0ull;
   for (int64_t v = lb * blockDim.x + threadIdx.x; v < nv; v += nblk * blockDim.x) {
     const float4 a = a4[v], m = m4[v];
-    part += (double)a.x * (double)m.x + (double)a.y * (double)m.y + (double)a.z * (double)m.z +
-            (double)a.w * (double)m.w;
+    dot2_acc2(f2_pack(a.x, a.y), f2_pack(-a.x, -a.y), f2_pack(m.x, m.y), hi0, lo0);
+    dot2_acc2(f2_pack(a.z, a.w), f2_pack(-a.z, -a.w), f2_pack(m.z, m.w), hi1, lo1);
+  }
+  const double part = ((double)f2_x(hi0) + (double)f2_y(hi0)) + ((double)f2_x(hi1) + (double)f2_y(hi1)) +
+                      (((double)f2_x(lo0) + (double)f2_y(lo0)) + ((double)f2_x(lo1) + (double)f2_y(lo1)));
+  // ||model||^2 = sum over (r, c) of prod_k (A_k^T A_k)_{rc}: this block's share of the entries
+  double mn = 0.0;
+  for (int64_t e = lb * blockDim.x + threadIdx.x; e < (int64_t)f.R * f.R; e += nblk * blockDim.x) {
+    const int r = (int)(e / f.R), c = (int)(e - (e / f.R) * f.R);
+    double p = 1.0;
+    for (int k = 0; k < f.N; ++k) p *= f.gram[k][r * f.Rp + c];
+    mn += p;
   }
   const double bs = block_sum(part, red);
+  const double bm = block_sum(mn, red);
   if (threadIdx.x == 0) {
-    f.part[lb] = bs;
+    f.part[2 * lb] = bs;
+    f.part[2 * lb + 1] = bm;
     __threadfence();
     const unsigned prev = atomicAdd(f.counter, 1u);
     amlast = (prev == (unsigned)nblk - 1u);
@@ -688,21 +701,16 @@ __global__ void __launch_bounds__(256) fit_kernel(const FitDesc* __restrict__ fd
   __syncthreads();
   if (amlast) {
     __threadfence();
-    double s = 0.0;
-    for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(f.part + b);
-    const double inner = block_sum(s, red);
-    double mn = 0.0;
-    for (int e = threadIdx.x; e < f.R * f.R; e += blockDim.x) {
-      const int r = e / f.R, c = e - (e / f.R) * f.R;
-      double p = 1.0;
-      for (int k = 0; k < f.N; ++k) p *= f.gram[k][r * f.Rp + c];
-      mn += p;
+    double s = 0.0, sm = 0.0;
+    for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) {
+      s += __ldcg(f.part + 2 * b);
+      sm += __ldcg(f.part + 2 * b + 1);
     }
-    const double mnorm = block_sum(mn, red);
+    const double inner = block_sum(s, red);
+    const double mnorm = block_sum(sm, red);
     if (threadIdx.x == 0) {
-      const double obj = f.norm_x_sq - 2.0 * inner + mnorm;
-      f.out[0] = obj;
-      f.out[1] = f.norm_x_sq > 0 ? 1.0 - sqrt(fmax(obj, 0.0)) / sqrt(f.norm_x_sq) : 0.0;
+      f.out[0] = f.norm_x_sq - 2.0 * inner + mnorm;  // the fit is formed on the host
+      f.out[1] = 0.0;
       f.out[2] = inner;
       f.out[3] = mnorm;
       *f.counter = 0u;
@@ -711,14 +719,15 @@ __global__ void __launch_bounds__(256) fit_kernel(const FitDesc* __restrict__ fd
 }
 
 // base[0..njobs]: prefix of the jobs' block counts (fit_blocks_for of their last mode)
+void launch_fit(const FitDesc* d_fit, const int64_t* d_base, int njobs, int64_t total_blocks, cudaStream_t st) {
+  fit_kernel<<<(unsigned)(total_blocks > 0 ? total_blocks : 1), 256, 0, st>>>(d_fit, d_base, njobs);
+}
+
 int64_t fit_blocks_for(int64_t I, int Rp) {
   const int64_t vecs = I * Rp / 4;
   return std::max<int64_t>(1, std::min<int64_t>((vecs + 1023) / 1024, 152 * 4));  // ~4 vectors per thread
 }
 
-void launch_fit(const FitDesc* d_fit, const int64_t* d_base, int njobs, int64_t total_blocks, cudaStream_t st) {
-  fit_kernel<<<(unsigned)(total_blocks > 0 ? total_blocks : 1), 256, 0, st>>>(d_fit, d_base, njobs);
-}
 
 // ------------------------------------------------------------------------------------------
 __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
