@@ -129,15 +129,23 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t
   counts[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
+// Stable scatter of one 8-bit digit. Each warp ranks its 256 keys per digit (match_any); the
+// block then places its keys in shared memory in digit order (block-local start of each digit
+// from a 256-entry scan, then the warps' shares, then the in-warp rank), and consecutive threads
+// write consecutive keys of each digit run to their global positions, so the writes coalesce.
 __global__ void __launch_bounds__(kSortThreads)
     radix_scatter_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t* kout,
                          uint32_t* vout, int64_t n, int shift, int64_t nb, const uint32_t* __restrict__ offs) {
   __shared__ uint32_t wcnt[kSortWarps][256];
   __shared__ uint32_t wbase[kSortWarps][256];
+  __shared__ uint32_t dstart[256];
+  __shared__ uint64_t skey[kSortTile];
+  __shared__ uint32_t sval[kSortTile];
   const int lane = lane_id(), w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)w * (32 * kSortRounds);
+  const int64_t blk0 = (int64_t)blockIdx.x * kSortTile;
+  const int64_t base = blk0 + (int64_t)w * (32 * kSortRounds);
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint64_t k[kSortRounds];
   uint32_t v[kSortRounds];
@@ -167,6 +175,28 @@ __global__ void __launch_bounds__(kSortThreads)
       wbase[ww][d] = run;
       run += wcnt[ww][d];
     }
+    dstart[d] = run;  // the block's count of digit d, scanned below
+  }
+  __syncthreads();
+  if (w == 0) {  // exclusive scan of the 256 counts: 8 consecutive digits per lane
+    uint32_t c[8], sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      c[i] = dstart[lane * 8 + i];
+      sum += c[i];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    uint32_t ex = incl - sum;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      dstart[lane * 8 + i] = ex;
+      ex += c[i];
+    }
   }
   __syncthreads();
 #pragma unroll
@@ -174,10 +204,19 @@ __global__ void __launch_bounds__(kSortThreads)
     const int64_t e = base + rd * 32 + lane;
     if (e < n) {
       const uint32_t d = dg[rd];
-      const uint32_t pos = offs[(int64_t)d * nb + blockIdx.x] + wbase[w][d] + rk[rd];
-      kout[pos] = k[rd];
-      vout[pos] = v[rd];
+      const uint32_t lp = dstart[d] + wbase[w][d] + rk[rd];
+      skey[lp] = k[rd];
+      sval[lp] = v[rd];
     }
+  }
+  __syncthreads();
+  const int cnt = (int)min((int64_t)kSortTile, n - blk0);
+  for (int t = threadIdx.x; t < cnt; t += kSortThreads) {
+    const uint64_t key = skey[t];
+    const uint32_t d = (uint32_t)((key >> shift) & 255u);
+    const uint32_t pos = offs[(int64_t)d * nb + blockIdx.x] + (uint32_t)t - dstart[d];
+    kout[pos] = key;
+    vout[pos] = sval[t];
   }
 }
 
