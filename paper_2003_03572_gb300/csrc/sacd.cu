@@ -172,7 +172,7 @@ struct TmpAllocs {
   std::vector<void*> p;
   explicit TmpAllocs(cudaStream_t s) : st(s) {}
   ~TmpAllocs() {
-    for (void* q : p) cudaFreeAsync(q, st);
+    for (auto it = p.rbegin(); it != p.rend(); ++it) cudaFreeAsync(*it, st);  // last in, first out
   }
   template <typename T>
   sacd_status get(T** out, size_t count) {
@@ -1341,7 +1341,7 @@ void sacd_destroy(sacd_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   invalidate_graph(c);
   for (auto& e : c->prof.ev) cudaEventDestroy(e);
-  for (void* p : c->allocs) cudaFreeAsync(p, c->st);
+  for (auto it = c->allocs.rbegin(); it != c->allocs.rend(); ++it) cudaFreeAsync(*it, c->st);  // last in, first out
   if (c->st) cudaStreamSynchronize(c->st);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
