@@ -5,6 +5,7 @@ the host (bad input, a job larger than the budget) finish only the failing job."
 import numpy as np
 import pytest
 
+from oracle import sacd_oracle as O
 from paper_2003_03572_gb300 import sacd as S
 from paper_2003_03572_gb300 import serve, synth
 
@@ -42,6 +43,28 @@ def test_served_results_equal_alone():
             for n in range(len(s["dims"])):
                 np.testing.assert_array_equal(F[n], a.factor(n))
             assert (r["objective"], r["fit"]) == a.fit()
+
+
+def test_served_jobs_match_oracle():
+    """Each served job against the FP64 oracle: FP32 jobs' final fits within 1e-4 (as for single
+    contexts); BF16-gather jobs against the oracle's BF16-gather definition within 5e-3 (rounding
+    the gathered rows flips selections, so trajectories drift slightly)."""
+    sp = specs(21)
+    iters = [6, 4, 5, 6, 3, 5]
+    with serve.Server(1 << 34) as srv:
+        ids = [srv.submit(s, it) for s, it in zip(sp, iters)]
+        done = {}
+        while len(done) < len(sp):
+            srv.step()
+            for r in srv.results():
+                assert r["status"] == 0, r
+                done[r["job_id"]] = r
+                srv.release(r["job_id"])
+    for jid, s, it in zip(ids, sp, iters):
+        bf16 = s["precision"] == S.SACD_BF16_GATHER
+        o = O.SaCDOracle(s["dims"], s["idx"], s["vals"], s["init"], gather="bf16" if bf16 else "fp32")
+        o.iterate(it)
+        assert abs(done[jid]["fit"] - o.fit()[1]) <= (5e-3 if bf16 else 1e-4)
 
 
 def test_budget_admission_and_host_failures():
