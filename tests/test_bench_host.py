@@ -59,6 +59,10 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["unit"] == "mode-steps/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    # per mode, the full-workload step time extrapolated from the two samples
+    ms = line["full_step_ms_by_mode"]
+    assert len(ms) == 3 and all(x > 0 for x in ms)
+    assert line["value"] == pytest.approx(3 / (sum(ms) / 1e3), rel=1e-3)
 
 
 def test_update_roofline_arithmetic():
