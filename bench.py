@@ -245,7 +245,7 @@ def reference_arm(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / args.steps,
-        "full_step_ms_by_mode": [round(float(x) * 1e3, 2) for x in full],
+        "full_step_ms_by_mode": [round(float(x) * 1e3, 4) for x in full],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,

@@ -62,7 +62,7 @@ def test_reference_arm_json_line():
     # per mode, the full-workload step time extrapolated from the two samples
     ms = line["full_step_ms_by_mode"]
     assert len(ms) == 3 and all(x > 0 for x in ms)
-    assert line["value"] == pytest.approx(3 / (sum(ms) / 1e3), rel=1e-3)
+    assert line["value"] == pytest.approx(3 / (sum(ms) / 1e3), rel=1e-2)
 
 
 def test_update_roofline_arithmetic():
