@@ -441,12 +441,12 @@ def ours_arm(args):
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
 
-def update_roofline(w, bf16, kernel_ms, steps, hbm_peak):
+def update_roofline(w, bf16, kernel_ms, steps, hbm_peak, compensated=False):
     """Select/update roofline of pass 1 + pass 2 (one element = one factor entry of a mode step):
     algorithmic bytes 20 per element (read M, A, z^{k-1}; write A, z^{k-1}; 22 with the BF16
-    mirror) against the HBM copy peak, and, for pass 1, which is bound by its compensated
-    products, 10 FP32 operations per product (exact product: 2, TwoSum: 6, error terms: 2) times R
-    products per element against the FP32 instruction peak."""
+    mirror) against the HBM copy peak, and, for pass 1, its R products per element against the FP32
+    instruction peak: one fused multiply-add each (Frobenius or spectral L, the bench's setting),
+    or 10 FP32 operations each when compensated (exact product 2, TwoSum 6, error terms 2; GCD)."""
     elems = sum(w.dims) * w.rank * steps
     bpe = 20 + (2 if bf16 else 0)
     t = (kernel_ms.get("pass1_grad_importance", 0.0) + kernel_ms.get("pass2_select_update", 0.0)) / 1e3
@@ -454,11 +454,12 @@ def update_roofline(w, bf16, kernel_ms, steps, hbm_peak):
     if t <= 0 or t1 <= 0:
         return None
     gbs = elems * bpe / t / 1e9
-    tops = elems * w.rank * 10 / t1 / 1e12
+    opp = 10 if compensated else 1
+    tops = elems * w.rank * opp / t1 / 1e12
     return {"kernels": ["pass1_grad_importance", "pass2_select_update"], "bytes_per_element": bpe,
             "elements_per_step": elems // steps, "achieved_gbs": gbs, "hbm_peak_gbs": hbm_peak,
             "frac_hbm": gbs / hbm_peak,
-            "pass1": {"bound": "alu", "ops_per_element": 10 * w.rank, "achieved_tops": tops,
+            "pass1": {"bound": "alu", "ops_per_element": opp * w.rank, "achieved_tops": tops,
                       "peak_tops": FP32_PEAK_TOPS, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
                       "frac": tops / FP32_PEAK_TOPS}}
 

@@ -67,7 +67,8 @@ def test_reference_arm_json_line():
 
 def test_update_roofline_arithmetic():
     """Select/update roofline: 20 B per element (22 with the BF16 mirror) over pass 1 + pass 2,
-    and 10 R FP32 operations per element over pass 1, against the stated peaks."""
+    and R FP32 operations per element over pass 1 (10 R when compensated), against the stated
+    peaks."""
     from paper_2003_03572_gb300 import synth
 
     w = synth.WORKLOADS["zipf1.1-50000x20000x500-5M-r32"]
@@ -77,7 +78,9 @@ def test_update_roofline_arithmetic():
     assert r["elements_per_step"] == E
     assert r["achieved_gbs"] == pytest.approx(4 * E * 20 / 5e-3 / 1e9)
     assert r["frac_hbm"] == pytest.approx(r["achieved_gbs"] / 6765.7)
-    assert r["pass1"]["achieved_tops"] == pytest.approx(4 * E * 32 * 10 / 2e-3 / 1e12)
+    assert r["pass1"]["achieved_tops"] == pytest.approx(4 * E * 32 / 2e-3 / 1e12)  # one FMA per product
+    rc = bench.update_roofline(w, False, km, 4, 6765.7, compensated=True)
+    assert rc["pass1"]["achieved_tops"] == pytest.approx(4 * E * 32 * 10 / 2e-3 / 1e12)
     assert r["pass1"]["peak_tops"] == pytest.approx(152 * 128 * 2.07e9 / 1e12)
     assert bench.update_roofline(w, True, km, 4, 6765.7)["bytes_per_element"] == 22
     assert bench.update_roofline(w, False, {}, 4, 6765.7) is None
