@@ -67,3 +67,44 @@ def test_bound_is_tight_where_nothing_cancels_and_catches_a_dropped_term():
     # a planted mistake: z without the (L/2) s^2 term
     wrong = -t["G"] * s
     assert (np.abs(wrong - z) > b).mean() > 0.5
+
+
+def _fma_order_ah_f32(A, H):
+    """A H in FP32, one rounding per product-accumulate, j ascending (the kernel's FMA chain)."""
+    A32 = A.astype(f32)
+    H32 = H.astype(f32)
+    acc = np.zeros((A.shape[0], H.shape[1]), np.float64)
+    for j in range(A.shape[1]):
+        acc = (acc + A32[:, j:j + 1].astype(np.float64) * H32[j:j + 1, :].astype(np.float64)).astype(f32)
+        acc = acc.astype(np.float64)
+    return acc
+
+
+def _worst_step_error(dims, nnz, R, lnorm, iters=2):
+    from paper_2003_03572_gb300 import synth
+
+    idx, vals = synth.sparse_tensor(dims, nnz, dist="zipf", zipf_s=1.1, seed=11)
+    o = O.SaCDOracle(dims, idx, vals, synth.init_factors(dims, R, 11), lnorm=lnorm)
+    worst = 0.0
+    for _ in range(iters):
+        for n in range(len(dims)):
+            A0 = o.A[n].copy()
+            o.mode_step(n)
+            t = o.last
+            g32 = (_fma_order_ah_f32(A0, t["H"]) - t["M"].astype(f32)).astype(f32).astype(np.float64)
+            A1, _ = O.update_rows(A0.copy(), g32, t["H"], t["sel"], "column_gs")
+            worst = max(worst, float(np.linalg.norm(A1 - o.A[n]) / np.linalg.norm(o.A[n])))
+    return worst
+
+
+def test_plain_fp32_gradient_meets_the_step_bound_except_for_gcd():
+    """The gradient G = A H - M summed in plain FP32 (fused multiply-adds, then one rounded
+    subtraction of M), with the oracle's selection replayed, keeps a mode step well inside the
+    1e-5 bound with the Frobenius or spectral L, but not with h_rr in place of L (Eq. 18), whose
+    larger and more numerous steps amplify the gradient error: that variant needs compensated
+    products."""
+    shapes = [((257, 129, 65), 7777, 64), ((300, 200, 40, 20), 20_000, 16)]
+    for dims, nnz, R in shapes:
+        assert _worst_step_error(dims, nnz, R, "fro") < 2e-6
+        assert _worst_step_error(dims, nnz, R, "spectral") < 2e-6
+    assert max(_worst_step_error(d, z, R, "gcd") for d, z, R in shapes) > 1e-5
