@@ -1378,9 +1378,8 @@ struct PlanMode {
   int njobs = 0;
   std::vector<sacd_ctx*> jobs;
   StepDesc* d_descs = nullptr;
-  int64_t *d_light = nullptr, *d_chunk = nullptr, *d_heavy = nullptr, *d_p1 = nullptr, *d_p2 = nullptr,
-          *d_gr = nullptr;
-  int64_t light = 0, chunk = 0, heavy = 0, p1 = 0, p2 = 0, gr = 0;
+  int64_t *d_chunk = nullptr, *d_p1 = nullptr, *d_p2 = nullptr, *d_gr = nullptr;
+  int64_t chunk = 0, p1 = 0, p2 = 0, gr = 0;  // (light rows and heavy rows' chunk sums: in pass 1)
   size_t smem = 0;
   std::vector<PlanClass> classes;
   std::vector<sacd_ctx*> empty_jobs;  // no nonzeros: M is zeroed instead of an MTTKRP
@@ -1432,15 +1431,13 @@ struct BatchPlan {
       PlanMode& pm = modes[n];
       pm = PlanMode();
       std::vector<StepDesc> descs;
-      std::vector<int64_t> light, chunk, heavy, p1, p2, gr;
+      std::vector<int64_t> chunk, p1, p2, gr;
       for (sacd_ctx* c : jobs) {
         if (n >= c->N) continue;
         pm.jobs.push_back(c);
         descs.push_back(c->hdesc[n]);
         const ModeData& md = c->m[n];
-        light.push_back(md.nlight);
         chunk.push_back(md.nchunks);
-        heavy.push_back(md.nheavy);
         p1.push_back(md.p1_blocks);
         p2.push_back(md.p2_blocks);
         gr.push_back(gram_reduce_blocks(c->Rp));
@@ -1450,12 +1447,10 @@ struct BatchPlan {
       pm.njobs = (int)pm.jobs.size();
       if (!pm.njobs) continue;
       auto tot = [](const std::vector<int64_t>& v) { int64_t s = 0; for (auto x : v) s += x; return s; };
-      pm.light = tot(light); pm.chunk = tot(chunk); pm.heavy = tot(heavy);
+      pm.chunk = tot(chunk);
       pm.p1 = tot(p1); pm.p2 = tot(p2); pm.gr = tot(gr);
       TRY(alloc_copy(&pm.d_descs, descs, st));
-      TRY(alloc_copy(&pm.d_light, prefix(light), st));
       TRY(alloc_copy(&pm.d_chunk, prefix(chunk), st));
-      TRY(alloc_copy(&pm.d_heavy, prefix(heavy), st));
       TRY(alloc_copy(&pm.d_p1, prefix(p1), st));
       TRY(alloc_copy(&pm.d_p2, prefix(p2), st));
       TRY(alloc_copy(&pm.d_gr, prefix(gr), st));
