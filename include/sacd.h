@@ -69,9 +69,9 @@ typedef struct {
   const float* vals;          /* nnz values (any sign; repeated coordinates are summed) */
   int32_t rank;               /* R, 1 <= R <= 256 */
   const float* const* init;   /* host array of N pointers to I_n x R row-major FP32, or NULL:
-                                 U[0,1) values (h >> 40) * 2^-24 drawn on the device, h the
-                                 splitmix64 finaliser of seed + (n+1)*0xD1B54A32D192ED03 +
-                                 (i*R + r + 1)*0x9E3779B97F4A7C15. Values must be finite, >= 0 */
+                                 U[0,1) values (h >> 40) * 2^-24 * 2^init_log2_scale drawn on the
+                                 device, h the splitmix64 finaliser of seed + (n+1)*0xD1B54A32D192ED03
+                                 + (i*R + r + 1)*0x9E3779B97F4A7C15. Values must be finite, >= 0 */
   uint64_t seed;              /* used only when init == NULL */
   int32_t precision;          /* sacd_precision */
   int32_t lnorm;              /* sacd_lnorm */
@@ -79,6 +79,8 @@ typedef struct {
   int32_t inputs_on_device;   /* 0: idx[n], vals, init[n] point to host memory;
                                  1: they point to device memory of the current device */
   void* stream;               /* cudaStream_t to run on, or NULL: the context creates its own */
+  int32_t init_log2_scale;    /* init == NULL only: every drawn value is scaled by 2^init_log2_scale
+                                 (exact), in [-60, 60]; 0 = U[0,1) */
 } sacd_config;
 
 /* Sizes and constants of a context (sacd_get_info). */
@@ -103,8 +105,8 @@ typedef struct {
  * order. Computes ||X||^2 and the FP64 Gram matrices A_k^T A_k of the initial factors.
  * Every factor starts "unvisited" (Algorithm 1, k == 1 branch).
  * On success *out receives the context; on error *out is set to NULL.
- * Errors: SACD_EINVAL (cfg ranges, an index outside [0, dims[n]), negative or non-finite init),
- * SACD_ENOMEM, SACD_ECUDA.
+ * Errors: SACD_EINVAL (cfg ranges, an index outside [0, dims[n]), negative or non-finite init,
+ * init_log2_scale out of range), SACD_ENOMEM, SACD_ECUDA.
  */
 sacd_status sacd_create(const sacd_config* cfg, sacd_ctx** out);
 
@@ -132,10 +134,14 @@ sacd_status sacd_iterate(sacd_ctx* ctx, int32_t iters);
  * ||X||^2 - 2<X, [[A]]> + sum_{r,s} prod_k (A_k^T A_k)_{rs}, in FP64, and
  * fit = 1 - sqrt(max(f, 0)) / ||X||. Waits for the stream. Either output pointer may be NULL.
  * The first call allocates a 32-byte pinned host buffer for the read-back, owned by the context.
+ * In the BF16-gather mode the cross term comes from FP32 gathers of the FP32 master factors (one
+ * extra MTTKRP per call), so the objective is that of the factors sacd_get_factor returns.
+ * Errors: SACD_ETIMEOUT (see sacd_set_wait_budget), SACD_ECUDA.
  */
 sacd_status sacd_fit(sacd_ctx* ctx, double* objective, double* fit);
 
-/* sacd_get_factor -- copy factor `mode` (I_n x R row-major FP32) to host_out. Waits. */
+/* sacd_get_factor -- copy factor `mode` (I_n x R row-major FP32) to host_out. Waits.
+ * Errors: SACD_EINVAL, SACD_ETIMEOUT (see sacd_set_wait_budget), SACD_ECUDA. */
 sacd_status sacd_get_factor(sacd_ctx* ctx, int32_t mode, float* host_out);
 
 /*
@@ -218,8 +224,20 @@ sacd_status sacd_load(sacd_ctx* ctx, const void* host_buf, size_t bytes);
 /* sacd_get_info -- sizes and constants of the context. */
 sacd_status sacd_get_info(sacd_ctx* ctx, sacd_info* out);
 
-/* sacd_sync -- wait for all work enqueued on the context's stream. */
+/* sacd_sync -- wait for all work enqueued on the context's stream. Errors: SACD_ETIMEOUT (see
+ * sacd_set_wait_budget), SACD_ECUDA. */
 sacd_status sacd_sync(sacd_ctx* ctx);
+
+/*
+ * sacd_set_wait_budget -- the bound, in SM clock cycles (default 2^31, about a second), of every
+ * wait inside the fused select/update kernel: its blocks meet at a grid barrier between the sum
+ * of z (ti, Eq. 25) and the selection (Eq. 24/27). A block that waits longer sets an error word
+ * and every block skips the update; the next call that waits for the stream (sacd_sync,
+ * sacd_fit, sacd_get_factor, sacd_mode_step with a count) returns SACD_ETIMEOUT and the context
+ * is poisoned. For tests of that path (a budget of a few cycles makes the wait run out).
+ * Errors: SACD_EINVAL (cycles < 1).
+ */
+sacd_status sacd_set_wait_budget(sacd_ctx* ctx, int64_t cycles);
 
 /*
  * Per-kernel timing. While enabled, mode steps and fits are launched one kernel at a time (no
@@ -253,14 +271,20 @@ sacd_status sacd_profile_read(sacd_ctx* ctx, sacd_kernel_stat* out, int32_t cap,
  *   M      output, I_mode x ld FP32 row-major, 16-byte aligned; every entry is written.
  * ld must be the padded rank, the next power of two >= max(8, rank). dims is a host array.
  * The work runs on `stream` (cudaStream_t, NULL = legacy default stream) and is not waited for.
+ * Preconditions on the device arrays, which this call cannot check without waiting for the GPU:
+ * every rowid[e] lies in [0, dims[mode]), every index of row j of cidx lies in [0, dims[k]) for
+ * the j-th other mode k, and rowid is sorted ascending. An index out of range makes the kernels
+ * read or write outside the caller's arrays; an unsorted rowid gives a wrong M.
  *
  * Scratch: a file-scope static device array of SACD_NOALLOC_SCRATCH_MIB MiB, held by every GPU
  * that loads the library until the process exits. A call needs 4 KiB + 2 * ceil(nnz / tile) *
  * ld * 4 bytes of it (tile = 32 / min(ld/4, 32) lane groups x 8..128 nonzeros, chosen from
  * nnz); larger problems are rejected with SACD_EINVAL before any GPU work. The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress), so make that first call
- * before any stream capture. Every call shares the array: calls that overlap on the GPU race.
- * Errors: SACD_EINVAL (ranges, null or misaligned pointers, too large), SACD_ECUDA.
+ * device looks up the array's device address (cudaGetSymbolAddress) and keeps it for the rest of
+ * the process, so make that first call before any stream capture, and do not use this entry
+ * point after a cudaDeviceReset of that device. Every call shares the array: calls that overlap
+ * on the GPU race. Errors: SACD_EINVAL (ranges, null or misaligned pointers, too large),
+ * SACD_ECUDA.
  */
 #define SACD_NOALLOC_SCRATCH_MIB 16
 sacd_status sacd_mttkrp_noalloc(int32_t nmodes, int32_t mode, const int64_t* dims, int64_t nnz,
@@ -301,8 +325,9 @@ void sacd_batch_destroy(sacd_batch* b);
  *    the whole budget finishes with SACD_ENOMEM; a job whose create fails finishes with that
  *    status), run one outer iteration of every admitted job with one batched launch set, and
  *    finish the jobs that reached their iteration count: objective and fit evaluated, factors
- *    copied to host memory, device memory freed. Waits for the GPU. Reports active and waiting
- *    counts (nullable).
+ *    copied to host memory, device memory freed (a job whose objective is not finite finishes
+ *    with SACD_ESTATE and no factors). Waits for the GPU. Reports active and waiting counts
+ *    (nullable).
  *  - sacd_server_results: drain up to `cap` finished jobs' results (times are seconds since the
  *    server was created, host clock); their factors stay available through
  *    sacd_server_get_factor (I_n x R FP32) until sacd_server_release.

@@ -27,7 +27,9 @@ design notes of the repository):
   start-of-step gradient).
 * N modes generalise the 3-mode text with Khatri-Rao / Hadamard products over all k != n and
   modes visited 0..N-1 in order (Gauss-Seidel across modes, as Algorithm 1 does U, V, W).
-* h_rr <= 0 (a zero column elsewhere): s = 0 and z = 0.
+* h_rr <= 0 (a zero column elsewhere), or h_rr numerically negligible, h_rr <= max(2^-40 max_j h_jj,
+  2^-126) (a rank-one component whose other-mode factors have collapsed: its exact step g/h_rr
+  grows without bound and leaves the FP32 range of the factors): s = 0 and z = 0.
 * G of Eq. 9 is half the derivative of f in Eq. 6; the factor cancels in g/h.
 * The objective sums over all cells (Eq. 7), so f = ||X||^2 - 2<X, M> + ||M||^2 with M the
   CP model; "fit" (not defined by the paper) is 1 - sqrt(max(f, 0)) / ||X||.
@@ -52,6 +54,7 @@ __all__ = [
     "mttkrp",
     "gram",
     "hadamard_of_grams",
+    "curvatures",
     "lipschitz",
     "gradient",
     "projected_delta",
@@ -179,6 +182,21 @@ def hadamard_of_grams(factors, n):
     return H
 
 
+H_REL_MIN = 2.0**-40  # h_rr below this share of the largest h_jj counts as zero
+H_ABS_MIN = 2.0**-126  # ... and so does any h_rr without a normal FP32 reciprocal
+
+
+def curvatures(H):
+    """The h_rr that the coordinate steps use (Eq. 11-13, 15): the diagonal of H, with every entry
+    <= max(H_REL_MIN * max_j h_jj, H_ABS_MIN) set to 0, so that such a column takes no step."""
+    h = np.array(np.diag(np.asarray(H, dtype=np.float64)), copy=True)
+    if h.size == 0:
+        return h
+    thr = max(H_REL_MIN * float(np.max(h)), H_ABS_MIN)
+    h[h <= thr] = 0.0
+    return h
+
+
 def lipschitz(H, norm="fro"):
     """L = ||H|| (Algorithm 1; proof of Lemma 1). Frobenius by the symbol table's ||.||."""
     if norm == "fro":
@@ -226,11 +244,12 @@ def select(Z, Zprev, ti, tiprev, first):
     return sp > 0
 
 
-def update_rows(A, G, H, sel, fixup="column_gs"):
+def update_rows(A, G, H, sel, fixup="column_gs", h=None):
     """Nonnegative coordinate update of the selected elements (Eq. 11-13), columns in order.
 
     For r = 0..R-1 (Algorithm 1's column loop), every selected u_qr with h_rr > 0 moves by
-    s = max(0, u_qr - g_qr/h_rr) - u_qr (Eq. 12) and u_qr += s (Eq. 13).
+    s = max(0, u_qr - g_qr/h_rr) - u_qr (Eq. 12) and u_qr += s (Eq. 13). ``h`` (default: the
+    diagonal of H) gives the h_rr of the steps (``curvatures``); the fix-up uses H itself.
     Gradient fix-up: "column_gs" adds s * H[r, :] to row q's gradient (the exact change of
     g_q = a_q H - m_q), "lemma2" changes g_qr alone (Lemma 2).
     Returns (new A, number of elements that were selected).
@@ -238,18 +257,19 @@ def update_rows(A, G, H, sel, fixup="column_gs"):
     A = np.array(A, dtype=np.float64, copy=True)
     g = np.array(G, dtype=np.float64, copy=True)
     R = A.shape[1]
+    hd = np.diag(H) if h is None else np.asarray(h, dtype=np.float64)
     for r in range(R):
-        h = H[r, r]
-        if not h > 0:
+        hr = hd[r]
+        if not hr > 0:
             continue
         rows = sel[:, r]
         s = np.zeros(A.shape[0])
-        s[rows] = np.maximum(0.0, A[rows, r] - g[rows, r] / h) - A[rows, r]
+        s[rows] = np.maximum(0.0, A[rows, r] - g[rows, r] / hr) - A[rows, r]
         A[:, r] += s
         if fixup == "column_gs":
             g += s[:, None] * H[r, :][None, :]
         elif fixup == "lemma2":
-            g[:, r] += s * h
+            g[:, r] += s * hr
         else:
             raise ValueError(fixup)
     return A, int(np.count_nonzero(sel))
@@ -373,7 +393,8 @@ class SaCDOracle:
         M = mttkrp(self.dims, self.idx, self.vals, gathered, n)  # Eq. 9, X_(n)(KRP)
         H = hadamard_of_grams(self.A, n)  # Eq. 10
         G = gradient(A, H, M)  # Eq. 9 / 14
-        h = np.diag(H)[None, :]
+        hd = curvatures(H)  # h_rr of the steps (negligible ones count as 0)
+        h = hd[None, :]
         if self.lnorm == "gcd":
             L = h  # Eq. 18: h_rr in place of L
         else:
@@ -387,7 +408,7 @@ class SaCDOracle:
             branch = "first" if self.first[n] else ("eq27" if ti > self.tiprev[n] else "eq24")
         else:
             sel = np.asarray(mask, dtype=bool)
-        Anew, nsel = update_rows(A, G, H, sel, self.fixup)  # Eq. 13 (+ fix-up)
+        Anew, nsel = update_rows(A, G, H, sel, self.fixup, hd)  # Eq. 13 (+ fix-up)
         self.last = dict(M=M, H=H, L=L, G=G, Z=Z, ti=ti, tiprev=self.tiprev[n], sel=sel, branch=branch,
                          first=self.first[n], Zprev=self.Zprev[n].copy(), Aold=A.copy())
         self.A[n] = Anew

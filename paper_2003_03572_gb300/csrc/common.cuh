@@ -69,27 +69,37 @@ struct StepDesc {
   int32_t lnorm;         // 0 Frobenius, 1 spectral, 2 GCD (h_rr)
   int32_t fixup;         // 0 column Gauss-Seidel, 1 Lemma 2
   int32_t p1_blocks;     // blocks of the row passes
+  int32_t sel_chunks;    // row chunks of the fused select/update kernel
+  int32_t _pad1;
   double* H;             // R x R FP64 (Rp stride)
   float* Hf;             // Rp x Rp FP32
   float* invh;           // Rp: 1/h_rr (0 where h_rr <= 0)
   float* lh;             // Rp: L/2 per column
   double* tipart;        // p1_blocks partial sums of z
   double* state;         // ST_STRIDE doubles of mode n
-  unsigned int* counters;  // [0] pass-1 blocks done, [1] gram blocks done, [2] fit blocks done
+  unsigned int* counters;  // [0] pass-1 blocks (or select/update chunks) done, [1] gram blocks done,
+                           // [2] fit blocks done
   unsigned long long* nsel;  // selected elements of the step
+};
+
+// Grid barrier words of one persistent launch (count, generation, error word: nonzero after a
+// bounded wait gave up).
+struct GridBar {
+  unsigned int count, gen, err, pad;
 };
 
 // Result of the objective evaluation (sacd_fit).
 struct FitDesc {
-  const float* A;        // factor N-1 (I x Rp)
-  const float* M;        // MTTKRP of mode N-1 with the current other factors
+  const float* A;        // the factor of the objective's mode (I x Rp)
+  const float* M;        // that mode's MTTKRP with the current other factors (FP32 gathers)
   int64_t I;
   int32_t R, Rp, N;
   const double* gram[SACD_MAXN];
   double norm_x_sq;
   double* part;          // per-block partials: 2 x blocks (<X, model>, ||model||^2)
-  double* out;           // [0] objective [1] unused [2] <X, model> [3] ||model||^2
+  double* out;           // [0] objective [1] wait-error word of the mode steps [2] <X, model> [3] ||model||^2
   unsigned int* counter;
+  const unsigned int* wait_err;  // GridBar::err of the launches that produced the factors (or null)
 };
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }

@@ -6,6 +6,7 @@
 
 struct StepDesc;
 struct FitDesc;
+struct GridBar;
 
 namespace sacd {
 
@@ -37,13 +38,25 @@ void launch_gram(const StepDesc* d_descs, const int64_t* d_base, int njobs, int6
 int gram_reduce_blocks(int Rp);
 void launch_gram_reduce(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks,
                         cudaStream_t st);
+// ---- fused select/update (selupd.cu): one cooperative launch per mode step (GCD uses pass1/pass2)
+__host__ __device__ int selupd_chunk_rows(int Rp, int rt);
+size_t selupd_smem_bytes(int Rp, int rt);
+int64_t selupd_chunks(int64_t I, int Rp, int rt);
+int selupd_choose_rt(int64_t rows, int Rp);  // rows per thread (1 or 4) for a launch over `rows` rows
+// smem: the largest selupd_smem_bytes over the launch's padded ranks (not monotonic in the rank);
+// the descriptors' sel_chunks must be those of `rt`
+cudaError_t launch_selupd(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_chunks, int rt,
+                          size_t smem, GridBar* bar, long long budget, cudaStream_t st);
+constexpr long long kWaitBudgetCycles = 1LL << 31;  // ~1 s at the maximum SM clock
+
 int64_t fit_blocks_for(int64_t I, int Rp);
 void launch_fit(const FitDesc* d_fit, const int64_t* d_base, int njobs, int64_t total_blocks, cudaStream_t st);
 void launch_to_bf16(const float* src, void* dst, int64_t n, cudaStream_t st);
 void launch_rmse(const int32_t* idx, const float* vals, int64_t n, const float* const* fac, int N, int R, int Rp,
                  double* part, int64_t blocks, double* out, unsigned int* counter, cudaStream_t st);
 void launch_pd(const double* gram, int R, int Rp, double* out, cudaStream_t st);
-void launch_init_factor(float* A, int64_t rows, int R, int Rp, unsigned long long seed, int mode, cudaStream_t st);
+void launch_init_factor(float* A, int64_t rows, int R, int Rp, unsigned long long seed, int mode, int log2_scale,
+                        cudaStream_t st);
 void launch_check_factor(const float* A, int64_t rows, int R, int Rp, unsigned int* bad, cudaStream_t st);
 
 // ---- preprocessing (prep.cu)

@@ -34,6 +34,11 @@ struct Head {
   int64_t tile_base;
 };
 
+// Writes the call's descriptor into the static array. The descriptor travels as a kernel
+// argument (copied when the launch is enqueued), so no host memory is read after this call
+// returns, and no host-to-device copy of a pageable stack object is needed.
+__global__ void put_head_kernel(Head h, Head* dst) { *dst = h; }
+
 // Rows split across tiles, found from the tile borders themselves (no precomputed list):
 // one block per border; the block of the first border a row crosses sums the row's partials
 // (slot 1 of its first tile, slot 0 of the following ones) with a fixed-shape tree.
@@ -178,8 +183,7 @@ sacd_status sacd_mttkrp_noalloc(int32_t nmodes, int32_t mode, const int64_t* dim
   d.N = nmodes;
   d.n = mode;
   h.tile_base = 0;
-  e = cudaMemcpyAsync(base, &h, sizeof(h), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return bad(SACD_ECUDA, cudaGetErrorString(e));
+  put_head_kernel<<<1, 1, 0, st>>>(h, reinterpret_cast<Head*>(base));
   const StepDesc* dd = reinterpret_cast<const StepDesc*>(base);
   const int64_t* tb = reinterpret_cast<const int64_t*>(base + offsetof(Head, tile_base));
   sacd::launch_mttkrp(dd, tb, 1, ntiles, 0, rv, nmodes - 1, st);

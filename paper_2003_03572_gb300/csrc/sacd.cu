@@ -29,9 +29,10 @@ sacd_status fail(sacd_status s, const std::string& msg) {
   return s;
 }
 
-enum KClass { K_HL = 0, K_MTTKRP, K_FIXUP, K_PASS1, K_PASS2, K_GRAM, K_FIT, K_NCLASS };
+enum KClass { K_HL = 0, K_MTTKRP, K_FIXUP, K_PASS1, K_PASS2, K_GRAM, K_FIT, K_FIT_MTTKRP, K_SELUPD, K_NCLASS };
 const char* kClassName[K_NCLASS] = {"hl", "mttkrp", "mttkrp_fixup", "pass1_grad_importance",
-                                    "pass2_select_update", "gram", "fit"};
+                                    "pass2_select_update", "gram", "fit", "fit_mttkrp",
+                                    "select_update"};
 
 struct ModeData {
   int64_t I = 0;
@@ -57,7 +58,8 @@ struct ModeData {
   float* zprev = nullptr;
   float* M = nullptr;
   double* gram = nullptr;
-  int64_t p1_blocks = 0, p2_blocks = 0, gram_blocks = 0;
+  int64_t p1_blocks = 0, p2_blocks = 0, gram_blocks = 0, sel_chunks = 0;
+  int sel_rt = 1;  // rows per thread of the fused select/update kernel for this mode
 };
 
 struct Prof {
@@ -108,10 +110,15 @@ struct sacd_ctx {
   double* tipart = nullptr;
   double* state = nullptr;
   unsigned int* counters = nullptr;
+  GridBar* bar = nullptr;             // grid barrier of the fused select/update launches
+  long long wait_budget = kWaitBudgetCycles;
+  unsigned int* wait_host = nullptr;  // pinned read-back of the barrier's error word
   unsigned long long* nsel = nullptr;
   int64_t* zero64 = nullptr;
-  StepDesc hdesc[SACD_MAXN];
+  StepDesc hdesc[SACD_MAXN + 1];  // [n] mode-n steps; [N] the objective's FP32-gather MTTKRP (BF16 mode)
   StepDesc* ddesc = nullptr;
+  float* Mfit = nullptr;  // BF16 mode: MTTKRP of mode fit_mode from the FP32 master factors (objective)
+  int fit_mode = 0;       // the mode whose M the objective contracts with its factor
   FitDesc hfit;
   FitDesc* dfit = nullptr;
   double* fitpart = nullptr;
@@ -235,28 +242,50 @@ struct KScope {
   ~KScope() { prof_record(c, cls, false); }
 };
 
-// With `fold`, pass 1 of the same mode step finishes the rows split across tiles (light rows and
-// the chunk sums of heavy rows, StepDesc::rowfix) and writes them into M, so only the chunk
-// level runs here; without it (M needed on its own, e.g. for the objective) every level runs.
-void enqueue_mttkrp(sacd_ctx* c, int n, bool fold) {
+// MTTKRP of mode n from descriptor `dd` (gathers of precision `prec`, `rv` 16-byte vectors per
+// row) into `Mout`, with the mode's tiling and split-row lists. With `fold`, pass 1 of the same
+// mode step finishes the rows split across tiles (light rows and the chunk sums of heavy rows,
+// StepDesc::rowfix) and writes them into M, so only the chunk level runs here; without it (M
+// needed on its own, e.g. for the objective) every level runs.
+void enqueue_mttkrp_desc(sacd_ctx* c, int n, const StepDesc* dd, int prec, int rv, float* Mout, bool fold,
+                         int cls_main, int cls_fix) {
   ModeData& md = c->m[n];
-  StepDesc* dd = c->ddesc + n;
   if (c->nnz == 0) {
-    cudaMemsetAsync(md.M, 0, (size_t)md.I * c->Rp * sizeof(float), c->st);
+    cudaMemsetAsync(Mout, 0, (size_t)md.I * c->Rp * sizeof(float), c->st);
     return;
   }
   {
-    KScope k(c, K_MTTKRP);
-    launch_mttkrp(dd, c->zero64, 1, md.ntiles, c->prec, c->rv, c->N - 1, c->st);
+    KScope k(c, cls_main);
+    launch_mttkrp(dd, c->zero64, 1, md.ntiles, prec, rv, c->N - 1, c->st);
   }
   if (md.nlight && !fold) {
-    KScope k(c, K_FIXUP);
+    KScope k(c, cls_fix);
     launch_fixup_light(dd, c->zero64, 1, md.nlight, c->st);
   }
   if (md.nheavy) {
-    KScope k(c, K_FIXUP);
+    KScope k(c, cls_fix);
     launch_fixup_chunks(dd, c->zero64, 1, md.nchunks, c->st);
     if (!fold) launch_fixup_heavy(dd, c->zero64, 1, md.nheavy, c->st);
+  }
+}
+
+void enqueue_mttkrp(sacd_ctx* c, int n, bool fold) {
+  enqueue_mttkrp_desc(c, n, c->ddesc + n, c->prec, c->rv, c->m[n].M, fold, K_MTTKRP, K_FIXUP);
+}
+
+// The M that the objective contracts with factor fit_mode (<X, model> = sum of A_n .* M_n for any
+// mode n). FP32 mode: the last mode's MTTKRP itself (recomputed only if a factor changed since the
+// last mode step). BF16-gather mode: an MTTKRP from FP32 gathers of the FP32 master factors (the
+// factors the caller gets back), into Mfit, every time: the BF16-gathered M of the mode steps is
+// not the model of those factors. It runs on the longest mode, whose other factors are the
+// smallest (the most gathered rows served from L1/L2).
+void enqueue_fit_mttkrp(sacd_ctx* c) {
+  if (c->prec == SACD_BF16_GATHER) {
+    enqueue_mttkrp_desc(c, c->fit_mode, c->ddesc + c->N, SACD_FP32, c->Rp / 4, c->Mfit, false, K_FIT_MTTKRP,
+                        K_FIT_MTTKRP);
+  } else if (!c->mlast_valid) {
+    enqueue_mttkrp(c, c->N - 1, false);
+    c->mlast_valid = true;
   }
 }
 
@@ -266,22 +295,35 @@ void enqueue_gram(sacd_ctx* c, int n) {
   launch_gram_reduce(c->ddesc + n, c->zero64, 1, gram_reduce_blocks(c->Rp), c->st);
 }
 
-void enqueue_step(sacd_ctx* c, int n) {
+// Gradient, importance, ti, selection and update of mode n: the fused cooperative kernel, or the
+// two row passes for the GCD variant (its compensated gradient is stored between them).
+void enqueue_select_update(sacd_ctx* c, int n, cudaStream_t st) {
   ModeData& md = c->m[n];
+  StepDesc* dd = c->ddesc + n;
+  if (c->lnorm != SACD_LNORM_GCD) {
+    KScope k(c, K_SELUPD);
+    launch_selupd(dd, c->zero64, 1, md.sel_chunks, md.sel_rt, selupd_smem_bytes(c->Rp, md.sel_rt), c->bar,
+                  c->wait_budget, st);
+    return;
+  }
+  {
+    KScope k(c, K_PASS1);
+    launch_pass1(dd, c->zero64, 1, md.p1_blocks, pass_smem_bytes(c->Rp), st);
+  }
+  {
+    KScope k(c, K_PASS2);
+    launch_pass2(dd, c->zero64, 1, md.p2_blocks, pass_smem_bytes(c->Rp), st);
+  }
+}
+
+void enqueue_step(sacd_ctx* c, int n) {
   StepDesc* dd = c->ddesc + n;
   {
     KScope k(c, K_HL);
     launch_hl(dd, 1, c->st);
   }
   enqueue_mttkrp(c, n, true);
-  {
-    KScope k(c, K_PASS1);
-    launch_pass1(dd, c->zero64, 1, md.p1_blocks, pass_smem_bytes(c->Rp), c->st);
-  }
-  {
-    KScope k(c, K_PASS2);
-    launch_pass2(dd, c->zero64, 1, md.p2_blocks, pass_smem_bytes(c->Rp), c->st);
-  }
+  enqueue_select_update(c, n, c->st);
   enqueue_gram(c, n);
 }
 
@@ -301,8 +343,7 @@ void enqueue_iteration_dag(sacd_ctx* c) {
     StepDesc* dd = c->ddesc + n;
     enqueue_mttkrp(c, n, true);
     cudaStreamWaitEvent(c->st, ev[1 + n], 0);
-    launch_pass1(dd, c->zero64, 1, md.p1_blocks, pass_smem_bytes(c->Rp), c->st);
-    launch_pass2(dd, c->zero64, 1, md.p2_blocks, pass_smem_bytes(c->Rp), c->st);
+    enqueue_select_update(c, n, c->st);
     cudaEventRecord(ev[N + 1 + n], c->st);
     cudaStreamWaitEvent(c->side, ev[N + 1 + n], 0);
     launch_gram(dd, c->zero64, 1, md.gram_blocks, c->Rp, c->side);
@@ -323,9 +364,31 @@ void invalidate_graph(sacd_ctx* c) {
   c->graph = nullptr;
 }
 
+// BF16 mode: the objective's MTTKRP of mode fit_mode gathers FP32 rows of the master factors. It
+// keeps the mode's tiles (same nonzeros per warp tile, so the same split-row lists and partial
+// buffers): the lane groups are half as many (FP32 rows are twice as wide), each with twice the
+// nonzeros.
+void fill_fit_desc(sacd_ctx* c) {
+  if (c->prec != SACD_BF16_GATHER) return;
+  const int L = c->fit_mode;
+  StepDesc d = c->hdesc[L];
+  d.prec = SACD_FP32;
+  d.rv = c->Rp / 4;
+  int o = 0;
+  for (int k = 0; k < c->N; ++k)
+    if (k != L) d.fac[o++] = c->m[k].A;
+  const int groups32 = 32 / std::min(d.rv, 32);
+  d.sub = d.tile / groups32;
+  d.M = c->Mfit;
+  d.mask = nullptr;
+  c->hdesc[c->N] = d;
+}
+
 sacd_status upload_descs(sacd_ctx* c) {
   for (int n = 0; n < c->N; ++n) c->hdesc[n].mask = c->debug ? c->mask : nullptr;
-  CK(cudaMemcpyAsync(c->ddesc, c->hdesc, sizeof(StepDesc) * c->N, cudaMemcpyHostToDevice, c->st));
+  fill_fit_desc(c);
+  const int nd = c->N + (c->prec == SACD_BF16_GATHER ? 1 : 0);
+  CK(cudaMemcpyAsync(c->ddesc, c->hdesc, sizeof(StepDesc) * nd, cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
   invalidate_graph(c);
   return SACD_OK;
@@ -334,6 +397,19 @@ sacd_status upload_descs(sacd_ctx* c) {
 // fit = 1 - sqrt(max(f, 0)) / ||X|| (0 for an all-zero tensor)
 double fit_from_objective(double objective, double norm_x_sq) {
   return norm_x_sq > 0 ? 1.0 - std::sqrt(std::max(objective, 0.0)) / std::sqrt(norm_x_sq) : 0.0;
+}
+
+// The error word of the fused select/update launches (a bounded grid-barrier wait gave up): read
+// at the calls that wait for the stream anyway. A step that gave up left its factor half updated,
+// so the context is poisoned.
+sacd_status check_wait(sacd_ctx* c) {
+  CK(cudaMemcpyAsync(c->wait_host, &c->bar->err, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (*c->wait_host) {
+    c->poisoned = true;
+    return fail(SACD_ETIMEOUT, "a bounded wait of the select/update kernel gave up (grid barrier)");
+  }
+  return SACD_OK;
 }
 
 sacd_status check_ctx(sacd_ctx* c) {
@@ -564,6 +640,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
   if (cfg->init)
     for (int n = 0; n < N; ++n)
       if (!cfg->init[n]) return fail(SACD_EINVAL, "null init[n]");
+  if (cfg->init_log2_scale < -60 || cfg->init_log2_scale > 60) return fail(SACD_EINVAL, "init_log2_scale must be in [-60, 60]");
 
   sacd_ctx* c = new (std::nothrow) sacd_ctx();
   if (!c) return fail(SACD_ENOMEM, "host allocation failed");
@@ -621,6 +698,14 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
   }
   TRY(dalloc(c, &c->counters, 8));
   CK(cudaMemsetAsync(c->counters, 0, 8 * sizeof(unsigned int), c->st));
+  TRY(dalloc(c, &c->bar, 1));
+  CK(cudaMemsetAsync(c->bar, 0, sizeof(GridBar), c->st));
+  {
+    void* h = nullptr;
+    CK(cudaMallocHost(&h, sizeof(unsigned int)));
+    c->wait_host = static_cast<unsigned int*>(h);
+    *c->wait_host = 0u;
+  }
   TRY(dalloc(c, &c->nsel, N));
   CK(cudaMemsetAsync(c->nsel, 0, N * sizeof(unsigned long long), c->st));
   int64_t* d_dims;
@@ -719,6 +804,8 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     chunks_max = std::max(chunks_max, md.nchunks);
     md.p1_blocks = (I + RB1 - 1) / RB1;
     md.p2_blocks = (I + RB2 - 1) / RB2;
+    md.sel_rt = selupd_choose_rt(I, Rp);
+    md.sel_chunks = selupd_chunks(I, Rp, md.sel_rt);
     md.gram_blocks = std::min<int64_t>((I + CH - 1) / CH, 4 * 152);
     p1_max = std::max(p1_max, md.p1_blocks);
     gb_max = std::max(gb_max, md.gram_blocks);
@@ -735,7 +822,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
       CK(cudaMemcpy2DAsync(md.A, sizeof(float) * Rp, cfg->init[n], sizeof(float) * R, sizeof(float) * R, I, k,
                            c->st));
     } else {
-      launch_init_factor(md.A, I, R, Rp, cfg->seed, n, c->st);
+      launch_init_factor(md.A, I, R, Rp, cfg->seed, n, cfg->init_log2_scale, c->st);
     }
     if (md.A16) launch_to_bf16(md.A, md.A16, I * Rp, c->st);
   }
@@ -767,7 +854,15 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
   CK(cudaMemsetAsync(c->H, 0, sizeof(double) * Rp * Rp, c->st));
 
   // ---- step descriptors
-  TRY(dalloc(c, &c->ddesc, N));
+  TRY(dalloc(c, &c->ddesc, N + 1));
+  c->fit_mode = N - 1;
+  if (c->prec == SACD_BF16_GATHER) {
+    for (int n = 0; n < N; ++n)
+      if (c->m[n].I > c->m[c->fit_mode].I || (c->m[n].I == c->m[c->fit_mode].I && n < c->fit_mode)) c->fit_mode = n;
+    const int64_t If = c->m[c->fit_mode].I;
+    TRY(dalloc(c, &c->Mfit, (size_t)If * Rp));
+    CK(cudaMemsetAsync(c->Mfit, 0, sizeof(float) * If * Rp, c->st));
+  }
   for (int n = 0; n < N; ++n) {
     ModeData& md = c->m[n];
     StepDesc& d = c->hdesc[n];
@@ -815,6 +910,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     d.lnorm = c->lnorm;
     d.fixup = c->fixup;
     d.p1_blocks = (int)md.p1_blocks;
+    d.sel_chunks = (int)md.sel_chunks;
     d.H = c->H;
     d.Hf = c->Hf;
     d.invh = c->invh;
@@ -827,7 +923,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
   TRY(upload_descs(c));
   // ---- fit descriptor
   {
-    const int L = N - 1;
+    const int L = c->fit_mode;
     c->fit_blocks = fit_blocks_for(c->m[L].I, c->Rp);
     TRY(dalloc(c, &c->fitpart, 2 * c->fit_blocks));
     TRY(dalloc(c, &c->fitout, 4));
@@ -840,7 +936,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     FitDesc& f = c->hfit;
     memset(&f, 0, sizeof(f));
     f.A = c->m[L].A;
-    f.M = c->m[L].M;
+    f.M = c->prec == SACD_BF16_GATHER ? c->Mfit : c->m[L].M;
     f.I = c->m[L].I;
     f.R = R;
     f.Rp = Rp;
@@ -850,6 +946,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     f.part = c->fitpart;
     f.out = c->fitout;
     f.counter = c->counters + 2;
+    f.wait_err = &c->bar->err;
     CK(cudaMemcpyAsync(c->dfit, &f, sizeof(f), cudaMemcpyHostToDevice, c->st));
   }
   // ---- initial Grams
@@ -901,7 +998,7 @@ sacd_status sacd_mode_step(sacd_ctx* c, int32_t mode, int64_t* n_selected) {
   if (n_selected) {
     unsigned long long v = 0;
     CK(cudaMemcpyAsync(&v, c->nsel + mode, sizeof(v), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
+    TRY(check_wait(c));
     *n_selected = (int64_t)v;
   }
   return SACD_OK;
@@ -935,10 +1032,7 @@ sacd_status sacd_iterate(sacd_ctx* c, int32_t iters) {
 
 sacd_status sacd_fit(sacd_ctx* c, double* objective, double* fit) {
   TRY(check_ctx(c));
-  if (!c->mlast_valid) {
-    enqueue_mttkrp(c, c->N - 1, false);
-    c->mlast_valid = true;
-  }
+  enqueue_fit_mttkrp(c);
   {
     KScope k(c, K_FIT);
     launch_fit(c->dfit, c->fitbase, 1, c->fit_blocks, c->st);
@@ -950,6 +1044,10 @@ sacd_status sacd_fit(sacd_ctx* c, double* objective, double* fit) {
   }
   CK(cudaMemcpyAsync(c->fit_host, c->fitout, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  if (c->fit_host[1] != 0.0) {
+    c->poisoned = true;
+    return fail(SACD_ETIMEOUT, "a bounded wait of the select/update kernel gave up (grid barrier)");
+  }
   if (objective) *objective = c->fit_host[0];
   if (fit) *fit = fit_from_objective(c->fit_host[0], c->norm_x_sq);
   return SACD_OK;
@@ -960,8 +1058,7 @@ sacd_status sacd_get_factor(sacd_ctx* c, int32_t mode, float* host_out) {
   if (mode < 0 || mode >= c->N || !host_out) return fail(SACD_EINVAL, "bad mode or null output");
   CK(cudaMemcpy2DAsync(host_out, sizeof(float) * c->R, c->m[mode].A, sizeof(float) * c->Rp, sizeof(float) * c->R,
                        c->m[mode].I, cudaMemcpyDeviceToHost, c->st));
-  CK(cudaStreamSynchronize(c->st));
-  return SACD_OK;
+  return check_wait(c);
 }
 
 sacd_status sacd_set_factor(sacd_ctx* c, int32_t mode, const float* host_in) {
@@ -1283,7 +1380,14 @@ sacd_status sacd_get_info(sacd_ctx* c, sacd_info* out) {
 
 sacd_status sacd_sync(sacd_ctx* c) {
   TRY(check_ctx(c));
-  CK(cudaStreamSynchronize(c->st));
+  return check_wait(c);
+}
+
+sacd_status sacd_set_wait_budget(sacd_ctx* c, int64_t cycles) {
+  TRY(check_ctx(c));
+  if (cycles < 1) return fail(SACD_EINVAL, "the wait budget must be at least one cycle");
+  c->wait_budget = cycles;
+  invalidate_graph(c);  // the budget is a kernel argument of the captured iteration
   return SACD_OK;
 }
 
@@ -1348,6 +1452,7 @@ void sacd_destroy(sacd_ctx* c) {
   if (c->side) cudaStreamDestroy(c->side);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   if (c->fit_host) cudaFreeHost(c->fit_host);
+  if (c->wait_host) cudaFreeHost(c->wait_host);
   cudaGetLastError();
   delete c;
 }
@@ -1378,8 +1483,11 @@ struct PlanMode {
   int njobs = 0;
   std::vector<sacd_ctx*> jobs;
   StepDesc* d_descs = nullptr;
-  int64_t *d_chunk = nullptr, *d_p1 = nullptr, *d_p2 = nullptr, *d_gr = nullptr;
-  int64_t chunk = 0, p1 = 0, p2 = 0, gr = 0;  // (light rows and heavy rows' chunk sums: in pass 1)
+  int64_t *d_chunk = nullptr, *d_p1 = nullptr, *d_p2 = nullptr, *d_gr = nullptr, *d_sel = nullptr;
+  int64_t chunk = 0, p1 = 0, p2 = 0, gr = 0, sel = 0;  // (light rows and heavy rows' chunk sums: in pass 1)
+  bool fused = true;  // no job uses the GCD variant: one fused select/update launch for all jobs
+  size_t sel_smem = 0;  // the largest shared memory need of the fused kernel over the jobs
+  int sel_rt = 1;       // its rows per thread
   size_t smem = 0;
   std::vector<PlanClass> classes;
   std::vector<sacd_ctx*> empty_jobs;  // no nonzeros: M is zeroed instead of an MTTKRP
@@ -1393,6 +1501,8 @@ struct BatchPlan {
   int64_t* d_fit_base = nullptr;
   int64_t fit_blocks = 0;
   double* d_fit_out = nullptr;  // njobs x 4
+  GridBar* d_bar = nullptr;      // grid barrier of the fused select/update launches
+  long long wait_budget = kWaitBudgetCycles;
   std::vector<void*> allocs;
   cudaStream_t alloc_st = nullptr;
 
@@ -1431,7 +1541,13 @@ struct BatchPlan {
       PlanMode& pm = modes[n];
       pm = PlanMode();
       std::vector<StepDesc> descs;
-      std::vector<int64_t> chunk, p1, p2, gr;
+      std::vector<int64_t> chunk, p1, p2, gr, sel;
+      // rows per thread of the mode's fused select/update launch: 4 when the jobs' 4-row chunks
+      // fill the GPU twice over
+      int64_t chunks4 = 0;
+      for (sacd_ctx* c : jobs)
+        if (n < c->N) chunks4 += selupd_chunks(c->m[n].I, c->Rp, 4);
+      pm.sel_rt = chunks4 >= 2 * 152 * 2 ? 4 : 1;
       for (sacd_ctx* c : jobs) {
         if (n >= c->N) continue;
         pm.jobs.push_back(c);
@@ -1441,6 +1557,10 @@ struct BatchPlan {
         p1.push_back(md.p1_blocks);
         p2.push_back(md.p2_blocks);
         gr.push_back(gram_reduce_blocks(c->Rp));
+        sel.push_back(selupd_chunks(md.I, c->Rp, pm.sel_rt));
+        descs.back().sel_chunks = (int)sel.back();
+        if (c->lnorm == SACD_LNORM_GCD) pm.fused = false;
+        pm.sel_smem = std::max(pm.sel_smem, selupd_smem_bytes(c->Rp, pm.sel_rt));
         pm.smem = std::max(pm.smem, pass_smem_bytes(c->Rp));
         if (c->nnz == 0) pm.empty_jobs.push_back(c);
       }
@@ -1448,8 +1568,9 @@ struct BatchPlan {
       if (!pm.njobs) continue;
       auto tot = [](const std::vector<int64_t>& v) { int64_t s = 0; for (auto x : v) s += x; return s; };
       pm.chunk = tot(chunk);
-      pm.p1 = tot(p1); pm.p2 = tot(p2); pm.gr = tot(gr);
+      pm.p1 = tot(p1); pm.p2 = tot(p2); pm.gr = tot(gr); pm.sel = tot(sel);
       TRY(alloc_copy(&pm.d_descs, descs, st));
+      TRY(alloc_copy(&pm.d_sel, prefix(sel), st));
       TRY(alloc_copy(&pm.d_chunk, prefix(chunk), st));
       TRY(alloc_copy(&pm.d_p1, prefix(p1), st));
       TRY(alloc_copy(&pm.d_p2, prefix(p2), st));
@@ -1496,7 +1617,11 @@ struct BatchPlan {
     for (auto x : fb) fit_blocks += x;
     std::vector<double> zeros((size_t)njobs * 4, 0.0);
     TRY(alloc_copy(&d_fit_out, zeros, st));
-    for (int j = 0; j < njobs; ++j) fds[j].out = d_fit_out + 4 * j;
+    TRY(alloc_copy(&d_bar, std::vector<GridBar>(1, GridBar{0u, 0u, 0u, 0u}), st));
+    for (int j = 0; j < njobs; ++j) {
+      fds[j].out = d_fit_out + 4 * j;
+      fds[j].wait_err = &d_bar->err;
+    }
     TRY(alloc_copy(&d_fit, fds, st));
     TRY(alloc_copy(&d_fit_base, prefix(fb), st));
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(SACD_ECUDA, "batch plan upload failed");
@@ -1514,8 +1639,12 @@ struct BatchPlan {
       for (const PlanClass& pc : pm.classes)
         launch_mttkrp(pc.d_descs, pc.d_tile_base, pc.njobs, pc.tiles, pc.prec, pc.rv, pc.nother, st);
       launch_fixup_chunks(pm.d_descs, pm.d_chunk, pm.njobs, pm.chunk, st);  // the rest is folded into pass 1
-      launch_pass1(pm.d_descs, pm.d_p1, pm.njobs, pm.p1, pm.smem, st);
-      launch_pass2(pm.d_descs, pm.d_p2, pm.njobs, pm.p2, pm.smem, st);
+      if (pm.fused) {
+        launch_selupd(pm.d_descs, pm.d_sel, pm.njobs, pm.sel, pm.sel_rt, pm.sel_smem, d_bar, wait_budget, st);
+      } else {
+        launch_pass1(pm.d_descs, pm.d_p1, pm.njobs, pm.p1, pm.smem, st);
+        launch_pass2(pm.d_descs, pm.d_p2, pm.njobs, pm.p2, pm.smem, st);
+      }
       for (const PlanClass& pc : pm.classes)
         launch_gram(pc.d_descs, pc.d_gram_base, pc.njobs, pc.gram_blocks, pc.Rp, st);
       launch_gram_reduce(pm.d_descs, pm.d_gr, pm.njobs, pm.gr, st);
@@ -1619,11 +1748,7 @@ sacd_status sacd_batch_iterate(sacd_batch* b, int32_t iters) {
 sacd_status sacd_batch_fit(sacd_batch* b, double* objective, double* fit) {
   if (!b) return fail(SACD_EINVAL, "null batch");
   if (b->poisoned) return fail(SACD_ESTATE, "batch is poisoned by an earlier CUDA error");
-  for (sacd_ctx* c : b->jobs)
-    if (!c->mlast_valid) {
-      enqueue_mttkrp(c, c->N - 1, false);
-      c->mlast_valid = true;
-    }
+  for (sacd_ctx* c : b->jobs) enqueue_fit_mttkrp(c);
   b->plan.enqueue_fit(b->st);
   std::vector<double> out((size_t)b->jobs.size() * 4);
   cudaError_t e = cudaMemcpyAsync(out.data(), b->plan.d_fit_out, sizeof(double) * out.size(), cudaMemcpyDeviceToHost,
@@ -1633,6 +1758,11 @@ sacd_status sacd_batch_fit(sacd_batch* b, double* objective, double* fit) {
     b->poisoned = true;
     return fail(SACD_ECUDA, std::string("batch fit: ") + cudaGetErrorString(e));
   }
+  for (size_t j = 0; j < b->jobs.size(); ++j)
+    if (out[4 * j + 1] != 0.0) {
+      b->poisoned = true;
+      return fail(SACD_ETIMEOUT, "a bounded wait of the select/update kernel gave up (grid barrier)");
+    }
   for (size_t j = 0; j < b->jobs.size(); ++j) {
     if (objective) objective[j] = out[4 * j];
     if (fit) fit[j] = fit_from_objective(out[4 * j], b->jobs[j]->norm_x_sq);
@@ -1860,6 +1990,19 @@ sacd_status sacd_server_step(sacd_server* s, int32_t* n_active, int32_t* n_waiti
     }
     s->plan.enqueue_iteration(s->st);
     s->steps++;
+    {
+      unsigned int h_err = 0;
+      cudaError_t e = cudaMemcpyAsync(&h_err, &s->plan.d_bar->err, sizeof(h_err), cudaMemcpyDeviceToHost, s->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+      if (e != cudaSuccess) {
+        s->poisoned = true;
+        return fail(SACD_ECUDA, std::string("server step: ") + cudaGetErrorString(e));
+      }
+      if (h_err) {
+        s->poisoned = true;
+        return fail(SACD_ETIMEOUT, "a bounded wait of the select/update kernel gave up (grid barrier)");
+      }
+    }
     std::vector<ServerJob*> still;
     for (ServerJob* j : s->active) {
       j->done_iters++;
@@ -1870,6 +2013,14 @@ sacd_status sacd_server_step(sacd_server* s, int32_t* n_active, int32_t* n_waiti
         continue;
       }
       sacd_status st = sacd_fit(j->ctx, &j->objective, &j->fit);
+      if (st == SACD_OK && !(std::isfinite(j->objective) && std::isfinite(j->fit))) {
+        // the job's arithmetic left the finite range: report it as a failed job, keep serving
+        j->status = SACD_ESTATE;
+        j->error = "objective is not finite: the factors left the FP32 range";
+        finish_job(s, j);
+        s->plan_dirty = true;
+        continue;
+      }
       if (st == SACD_OK) {
         j->factors.resize(j->ctx->N);
         for (int n = 0; n < j->ctx->N && st == SACD_OK; ++n) {

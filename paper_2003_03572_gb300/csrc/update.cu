@@ -15,30 +15,9 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "rowpass.cuh"
 
 namespace sacd {
-
-// ------------------------------------------------------------------------------------------
-// block reductions with a fixed shape (deterministic)
-// (warp butterflies, then the warps' sums in warp order; `red` holds at least 33 entries)
-template <typename T>
-__device__ T block_sum(T v, T* red) {
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    T r = l < (int)(blockDim.x >> 5) ? red[l] : T(0);
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-    if (l == 0) red[32] = r;
-  }
-  __syncthreads();
-  const T r = red[32];
-  __syncthreads();
-  return r;
-}
 
 // ------------------------------------------------------------------------------------------
 // H, L, 1/h, L/2
@@ -87,13 +66,30 @@ __global__ void __launch_bounds__(256) hl_kernel(const StepDesc* __restrict__ de
     }
     L = lam;
   }
+  // h_rr of the coordinate steps; an h_rr at or below max(2^-40 max_j h_jj, 2^-126) counts as 0
+  // (a column whose other-mode factors have collapsed takes no step: its exact step g/h_rr
+  // would leave the FP32 range, and 1/h_rr must stay a finite FP32 value)
+  double hmax = 0.0;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double h = 1.0;
+    for (int k = 0; k < N; ++k)
+      if (k != n) h *= __ldg(grams[k] + r * Rp + r);
+    v[r] = h;
+    hmax = fmax(hmax, h);
+  }
+  red[threadIdx.x] = hmax;
+  __syncthreads();
+  for (int w = blockDim.x >> 1; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  const double hthr = fmax(0x1p-40 * red[0], 0x1p-126);
+  __syncthreads();
   for (int r = threadIdx.x; r < Rp; r += blockDim.x) {
     float ih = 0.f, lhv = 0.f;
     if (r < R) {
-      double h = 1.0;
-      for (int k = 0; k < N; ++k)
-        if (k != n) h *= __ldg(grams[k] + r * Rp + r);
-      if (h > 0.0) ih = (float)(1.0 / h);
+      const double h = v[r];
+      if (h > hthr) ih = (float)(1.0 / h);
       lhv = (float)(0.5 * (lnorm == 2 ? h : L));
     }
     dp->invh[r] = ih;
@@ -121,79 +117,6 @@ size_t pass_smem_bytes(int Rp) {
   b += (size_t)RB * 32;                                // selection bytes (pass 2)
   b += (size_t)2 * Rp * sizeof(float);                 // 1/h_rr and L/2 (pass 2)
   return (b + 15) / 16 * 16;
-}
-
-// stage `nrows` rows of an I x Rp matrix into shared memory with row stride Rp+1
-__device__ __forceinline__ void stage_rows(const float* __restrict__ src, float* dst, int nrows, int Rp) {
-  const int ST = Rp + 1;
-  const float4* s4 = reinterpret_cast<const float4*>(src);
-  const int n4 = nrows * Rp / 4;
-  for (int e = threadIdx.x; e < n4; e += blockDim.x) {
-    const float4 v = s4[e];
-    const int f = e * 4;
-    const int r = f / Rp, c = f - r * Rp;
-    float* p = dst + r * ST + c;
-    p[0] = v.x; p[1] = v.y; p[2] = v.z; p[3] = v.w;
-  }
-}
-
-// compensated (hi, lo) accumulation of a*b
-__device__ __forceinline__ void dot2_acc(float a, float b, float& hi, float& lo) {
-  float p, e, s, t;
-  two_prod(a, b, p, e);
-  two_sum(hi, p, s, t);
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(t, e));
-}
-
-// ------------------------------------------------------------------------------------------
-// A row of M split across MTTKRP tiles, finished from the partials (columns c0 .. c0+7): a light
-// row sums slot 1 of its first tile and slot 0 of the following tiles in tile order (the order of
-// the separate light fix-up), a heavy row its chunk sums in chunk order.
-__device__ __forceinline__ void split_row_sum(const StepDesc* __restrict__ dp, int32_t fx, int c0, float4& m0,
-                                              float4& m1) {
-  const int nvec = dp->Rp >> 2, v0 = c0 >> 2;
-  const float4* __restrict__ src;
-  int64_t first, count, stride;
-  if (fx >= 0) {
-    const int4 s = dp->split_light[fx];  // {row, first tile, last tile, 0}
-    src = reinterpret_cast<const float4*>(dp->carry);
-    m0 = src[((int64_t)s.y * 2 + 1) * nvec + v0];
-    m1 = src[((int64_t)s.y * 2 + 1) * nvec + v0 + 1];
-    first = (int64_t)s.y * 2 + 2;  // slot 0 of tile s.y + 1
-    count = (int64_t)s.z - s.y;
-    stride = 2 * (int64_t)nvec;
-  } else {
-    const int4 s = dp->split_heavy[-2 - fx];  // {row, first chunk, chunk count, 0}
-    src = reinterpret_cast<const float4*>(dp->carry2);
-    m0 = src[(int64_t)s.y * nvec + v0];
-    m1 = src[(int64_t)s.y * nvec + v0 + 1];
-    first = (int64_t)s.y + 1;
-    count = (int64_t)s.z - 1;
-    stride = nvec;
-  }
-  // four partials' loads in flight at a time, added in order
-  int64_t k = 0;
-  for (; k + 4 <= count; k += 4) {
-    float4 a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t o = first * nvec + (k + i) * stride;
-      a[i] = src[o + v0];
-      b[i] = src[o + v0 + 1];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      m0.x += a[i].x; m0.y += a[i].y; m0.z += a[i].z; m0.w += a[i].w;
-      m1.x += b[i].x; m1.y += b[i].y; m1.z += b[i].z; m1.w += b[i].w;
-    }
-  }
-  for (; k < count; ++k) {
-    const int64_t o = first * nvec + k * stride;
-    const float4 a = src[o + v0], b = src[o + v0 + 1];
-    m0.x += a.x; m0.y += a.y; m0.z += a.z; m0.w += a.w;
-    m1.x += b.x; m1.y += b.y; m1.z += b.z; m1.w += b.w;
-  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -735,7 +658,7 @@ __global__ void __launch_bounds__(256) fit_kernel(const FitDesc* __restrict__ fd
     const double mnorm = block_sum(sm, red);
     if (threadIdx.x == 0) {
       f.out[0] = f.norm_x_sq - 2.0 * inner + mnorm;  // the fit is formed on the host
-      f.out[1] = 0.0;
+      f.out[1] = f.wait_err ? (double)*(volatile const unsigned int*)f.wait_err : 0.0;
       f.out[2] = inner;
       f.out[3] = mnorm;
       *f.counter = 0u;
@@ -856,11 +779,12 @@ void launch_pd(const double* gram, int R, int Rp, double* out, cudaStream_t st) 
   pd_kernel<<<1, 256, 0, st>>>(gram, R, Rp, out);
 }
 
-// U[0,1) initial factor values (h >> 40) * 2^-24, where h is the splitmix64 finaliser of
-// seed + (mode + 1) * 0xD1B54A32D192ED03 + (element + 1) * 0x9E3779B97F4A7C15 (a counter-based
-// generator: every element is drawn independently, so the draw is the same on any grid).
+// U[0,1) initial factor values (h >> 40) * 2^-24, times 2^log2_scale (exact), where h is the
+// splitmix64 finaliser of seed + (mode + 1) * 0xD1B54A32D192ED03 + (element + 1) * 0x9E3779B97F4A7C15
+// (a counter-based generator: every element is drawn independently, so the draw is the same on any
+// grid).
 __global__ void init_factor_kernel(float* __restrict__ A, int64_t rows, int R, int Rp, unsigned long long seed,
-                                   int mode) {
+                                   int mode, int log2_scale) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * R;
        e += (int64_t)gridDim.x * blockDim.x) {
     unsigned long long z = seed + (unsigned long long)(mode + 1) * 0xD1B54A32D192ED03ull +
@@ -870,13 +794,14 @@ __global__ void init_factor_kernel(float* __restrict__ A, int64_t rows, int R, i
     z ^= z >> 31;
     const int64_t i = e / R;
     const int r = (int)(e - i * R);
-    A[i * Rp + r] = (float)(z >> 40) * (1.0f / 16777216.0f);
+    A[i * Rp + r] = ldexpf((float)(z >> 40), log2_scale - 24);
   }
 }
-void launch_init_factor(float* A, int64_t rows, int R, int Rp, unsigned long long seed, int mode, cudaStream_t st) {
+void launch_init_factor(float* A, int64_t rows, int R, int Rp, unsigned long long seed, int mode, int log2_scale,
+                        cudaStream_t st) {
   if (rows * R <= 0) return;
   const int64_t blocks = min((rows * R + 255) / 256, (int64_t)152 * 16);
-  init_factor_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, rows, R, Rp, seed, mode);
+  init_factor_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, rows, R, Rp, seed, mode, log2_scale);
 }
 
 __global__ void check_factor_kernel(const float* __restrict__ A, int64_t rows, int R, int Rp,

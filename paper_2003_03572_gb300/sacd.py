@@ -42,6 +42,7 @@ __all__ = [
     "sacd_save",
     "sacd_load",
     "sacd_sync",
+    "sacd_set_wait_budget",
     "sacd_profile_enable",
     "sacd_profile_read",
     "sacd_mttkrp_noalloc",
@@ -92,6 +93,7 @@ class sacd_config(C.Structure):
         ("fixup", C.c_int32),
         ("inputs_on_device", C.c_int32),
         ("stream", C.c_void_p),
+        ("init_log2_scale", C.c_int32),
     ]
 
 
@@ -176,6 +178,7 @@ def lib():
         "sacd_save": (C.c_int, [vp, vp, C.c_size_t, C.POINTER(C.c_size_t)]),
         "sacd_load": (C.c_int, [vp, vp, C.c_size_t]),
         "sacd_sync": (C.c_int, [vp]),
+        "sacd_set_wait_budget": (C.c_int, [vp, i64]),
         "sacd_profile_enable": (C.c_int, [vp, i32]),
         "sacd_profile_read": (C.c_int, [vp, C.POINTER(sacd_kernel_stat), i32, C.POINTER(i32)]),
         "sacd_mttkrp_noalloc": (C.c_int, [i32, i32, C.POINTER(i64), i64, vp, vp, vp, C.POINTER(vp), i32, i32, vp, vp]),
@@ -220,7 +223,7 @@ def _ptr(a):
 
 
 def _make_config(dims, idx, vals, rank, init=None, *, seed=0, precision=SACD_FP32, lnorm=SACD_LNORM_FRO,
-                 fixup=SACD_FIXUP_COLUMN_GS, stream=None, on_device=False):
+                 fixup=SACD_FIXUP_COLUMN_GS, stream=None, on_device=False, init_log2_scale=0):
     """A sacd_config plus the Python objects that must stay alive while it is used."""
     N = len(dims)
     keep = []
@@ -252,6 +255,7 @@ def _make_config(dims, idx, vals, rank, init=None, *, seed=0, precision=SACD_FP3
     cfg.fixup = int(fixup)
     cfg.inputs_on_device = 1 if on_device else 0
     cfg.stream = stream
+    cfg.init_log2_scale = int(init_log2_scale)
     keep += [dims_a, idx_p, init_p]
     return cfg, keep
 
@@ -438,6 +442,10 @@ def sacd_load(ctx, state):
 
 def sacd_sync(ctx):
     _check(lib().sacd_sync(ctx))
+
+
+def sacd_set_wait_budget(ctx, cycles):
+    _check(lib().sacd_set_wait_budget(ctx, int(cycles)))
 
 
 def sacd_profile_enable(ctx, on):

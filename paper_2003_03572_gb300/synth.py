@@ -20,7 +20,9 @@ Recipe (every draw comes from ``numpy.random.Generator(PCG64(seed))``):
 * Values: uniform integers 1..5 as FP32, or lognormal(0, 1) rounded to FP32.
 * The nonzeros come out in a seeded random order (COO is unsorted on purpose).
 * Initial factors: U[0, 1) drawn as ``k * 2^-24`` with k uniform in [0, 2^24), so each value
-  is exact in FP32 and FP64 and both sides start from identical numbers.
+  is exact in FP32 and FP64 and both sides start from identical numbers. The batched and served
+  workloads scale them by a power of two (exact) chosen so that the initial CP model's expected
+  norm matches the tensor's (``init_log2_scale``); the other workloads use U[0, 1) as drawn.
 """
 
 from __future__ import annotations
@@ -39,6 +41,7 @@ __all__ = [
     "make_workload",
     "batched_workloads",
     "serving_workloads",
+    "init_log2_scale",
 ]
 
 _I32_MAX = 2**31 - 1
@@ -162,14 +165,28 @@ def sparse_tensor(dims, nnz, *, dist="uniform", zipf_s=1.1, values="int15", seed
     return np.ascontiguousarray(idx.astype(np.int32)), vals
 
 
-def init_factors(dims, rank, seed):
-    """Nonnegative U[0,1) initial factors, each value k*2^-24 (exact in FP32 and FP64)."""
+def init_factors(dims, rank, seed, log2_scale=0):
+    """Nonnegative U[0,1) initial factors, each value k*2^-24 (exact in FP32 and FP64), times
+    2^log2_scale (still exact)."""
     rng = _rng(seed ^ 0x1F1F1F1F)
     out = []
     for d in dims:
         k = rng.integers(0, 2**24, size=(int(d), int(rank)))
-        out.append(np.ascontiguousarray((k * 2.0**-24).astype(np.float32)))
+        out.append(np.ascontiguousarray((k * 2.0 ** (int(log2_scale) - 24)).astype(np.float32)))
     return out
+
+
+def init_log2_scale(dims, rank, nnz, mean_sq=11.0):
+    """Power-of-two scale of U[0,1) initial factors that brings the initial model's expected squared
+    norm to the tensor's expected squared norm, nnz * mean_sq (11 for uniform integers 1..5). With
+    U[0,1) entries a factor's Gram averages I/3 on its diagonal and I/4 off it, so the model's
+    squared norm (the sum over r, s of the product of the Grams) averages about
+    R prod_k I_k/3 + R (R-1) prod_k I_k/4; each of the N factors takes an equal share of the scale.
+    An input recipe only: nothing here is part of the factorisation."""
+    N = len(dims)
+    m0 = rank * math.prod(d / 3.0 for d in dims) + rank * (rank - 1) * math.prod(d / 4.0 for d in dims)
+    c = math.sqrt(max(nnz, 1) * mean_sq / m0) ** (1.0 / N)
+    return int(round(math.log2(c)))
 
 
 @dataclasses.dataclass(frozen=True)
@@ -186,6 +203,7 @@ class Workload:
     iters: int
     precision: str  # "fp32" or "bf16"
     seed: int
+    init_log2: int = 0  # initial factors U[0,1) * 2^init_log2
 
     @property
     def nmodes(self):
@@ -243,7 +261,8 @@ def batched_workloads(njobs=512, seed=0x5ACD0003, nnz_range=(10_000, 500_000), r
         nnz = min(nnz, math.prod(dims) // 2)
         rank = int(rng.choice(ranks))
         jobs.append(
-            Workload(f"job{j}", dims, nnz, "zipf", 1.1, "int15", rank, iters, "fp32", seed * 1000003 + j)
+            Workload(f"job{j}", dims, nnz, "zipf", 1.1, "int15", rank, iters, "fp32", seed * 1000003 + j,
+                     init_log2_scale(dims, rank, nnz))
         )
     return jobs
 
@@ -251,7 +270,8 @@ def batched_workloads(njobs=512, seed=0x5ACD0003, nnz_range=(10_000, 500_000), r
 def serving_workloads(njobs, seed=0x5ACD0004, pool=None, iters=30):
     """Jobs of the served workload: N in {3, 4} (p = 1/2 each), every mode length log-uniform in
     [500, 100000], nnz log-uniform in [50k, 5M] (at most half the cells), Zipf(1.1) coordinates,
-    R uniform from {16, 32, 64}, BF16 gathers, `iters` iterations.
+    R uniform from {16, 32, 64}, BF16 gathers, `iters` iterations. Each job's initial factors are
+    drawn on the device from its seed, scaled by 2^init_log2_scale(dims, R, nnz).
 
     With ``pool`` = P, only P distinct tensors are drawn and job i uses tensor i % P (its own rank
     and initial factors): a stand-in that keeps the shape and size mix while bounding the time

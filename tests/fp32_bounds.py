@@ -18,7 +18,7 @@ def z_fp32_bound(a, t):
     exceeds any fixed fraction of max |z|."""
     a = np.asarray(a, np.float64)
     g = t["G"]
-    h = np.diag(t["H"])
+    h = O.curvatures(t["H"])
     L = np.broadcast_to(np.asarray(t["L"], np.float64), g.shape)
     s = O.projected_delta(a, g, h)
     inv = np.where(h > 0, 1.0 / np.where(h > 0, h, 1.0), 0.0)

@@ -84,6 +84,10 @@ def test_update_roofline_arithmetic():
     assert r["pass1"]["peak_tops"] == pytest.approx(152 * 128 * 2.07e9 / 1e12)
     assert bench.update_roofline(w, True, km, 4, 6765.7)["bytes_per_element"] == 22
     assert bench.update_roofline(w, False, {}, 4, 6765.7) is None
+    # the fused kernel: both phases form A H (2R FMAs per element)
+    rf = bench.update_roofline(w, False, {"select_update": 1.0}, 4, 6765.7)
+    assert rf["achieved_gbs"] == pytest.approx(4 * E * 20 / 1e-3 / 1e9)
+    assert rf["select_update"]["achieved_tops"] == pytest.approx(4 * E * 64 / 1e-3 / 1e12)
 
 
 def test_traffic_is_per_workload_and_per_kernel_source():

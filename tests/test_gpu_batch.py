@@ -55,3 +55,23 @@ def test_batch_fits_match_oracle():
         o = O.SaCDOracle(sp["dims"], sp["idx"], sp["vals"], sp["init"])
         o.iterate(K)
         assert abs(fit[j] - o.fit()[1]) <= 1e-4
+
+
+def test_batch_of_small_ranks_only():
+    """A batch whose jobs have padded ranks 16 and 8 only. The fused select/update kernel's shared
+    memory need is not monotonic in the rank (rank 8 takes 1024-row chunks and more memory than
+    rank 16), so one launch for both must be sized by the larger need, not by the larger rank.
+    Results bit-identical to the jobs run alone."""
+    specs = []
+    for j, (dims, R) in enumerate([((300, 200, 50), 16), ((200, 220, 60), 8), ((1500, 90, 30), 8)]):
+        idx, vals = synth.sparse_tensor(dims, 5000 + 2000 * j, dist="zipf", zipf_s=1.1, seed=40 + j)
+        specs.append(dict(dims=dims, idx=idx, vals=vals, rank=R, init=synth.init_factors(dims, R, 40 + j)))
+    with S.SaCDBatch(specs) as b:
+        b.iterate(3)
+        obj, fit = b.fit()
+        for j, sp in enumerate(specs):
+            with S.SaCD(sp["dims"], sp["idx"], sp["vals"], sp["rank"], sp["init"]) as a:
+                a.iterate(3)
+                for n in range(3):
+                    np.testing.assert_array_equal(b.factor(j, n), a.factor(n))
+                assert (obj[j], fit[j]) == a.fit()

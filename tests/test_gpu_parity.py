@@ -10,8 +10,12 @@ Tolerances (written here, from the stated targets):
 * free selection: every element where the GPU and the oracle disagree must sit at the decision
   boundary, |sp_oracle| <= 1e-5 max|z| (or the ti comparison is within 1e-6 sum|z|).
 * final fit after K iterations: |delta fit| <= 1e-4 (FP32). BF16 gathers: the mode step matches
-  the oracle's BF16-gather definition within 1e-5; the final fit against the FP64 oracle is
-  bounded by 5e-3 (not the 1e-3 target: BF16 rounding alone flips selections, see the test).
+  the oracle's BF16-gather definition within 1e-5; each of 30 iterations, from the GPU's state
+  with its selection replayed, ends within 1e-3 of the oracle's fit; the free 30-iteration
+  trajectory within 5e-3 (twice the spread of two oracle runs that differ only by FP32 rounding
+  of the factors, see the test).
+* objective at identical factors: 2e-6 of 2<X, model> (FP32 MTTKRP behind the cross term) plus
+  1e-9 of ||model||^2 (FP64 Grams), in both precisions.
 """
 
 import json
@@ -34,6 +38,24 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 def relerr(a, b):
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / (nb if nb > 0 else 1.0))
+
+
+def assert_elementwise(got, ref, tol, scale_rows=None):
+    """|got - ref| <= tol (|ref| + s_q) for every element of row q, s_q = max |ref| of the row (or the
+    given per-row scale), so that a wrong value in a light row cannot hide under heavy rows."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    s = np.abs(ref).max(axis=1, keepdims=True) if scale_rows is None else np.asarray(scale_rows)[:, None]
+    bad = np.abs(got - ref) > tol * (np.abs(ref) + s)
+    assert not bad.any(), f"{int(bad.sum())} elements off, first at {np.argwhere(bad)[0]}"
+
+
+def assert_rowwise(got, ref, tol, floor_rows):
+    """Per row: ||got_q - ref_q|| <= tol max(||ref_q||, floor_q)."""
+    d = np.linalg.norm(np.asarray(got, np.float64) - ref, axis=1)
+    s = np.maximum(np.linalg.norm(ref, axis=1), floor_rows)
+    bad = d > tol * s
+    assert not bad.any(), f"{int(bad.sum())} rows off, first {np.flatnonzero(bad)[0]}"
 
 
 # dims, nnz, dist, zipf s, rank: several tiles per mode, a ragged tail, hot rows split across
@@ -106,12 +128,16 @@ def test_mttkrp_gram_and_mode_step_replay(case):
                 mask = g.tap("MASK", n, last_mode=n).astype(bool)
                 o.mode_step(n, mask=mask)
                 t = o.last
-                assert relerr(g.tap("M", n), t["M"]) <= 1e-5
+                Mg = g.tap("M", n)
+                assert relerr(Mg, t["M"]) <= 1e-5
+                assert_elementwise(Mg, t["M"], 1e-5)
                 H = t["H"]
                 assert relerr(g.tap("H", n, last_mode=n), H) <= 1e-10
                 Gg = g.tap("G", n, last_mode=n)
-                den = np.linalg.norm(t["M"]) + np.linalg.norm(F[n].astype(np.float64) @ H)
+                AH = F[n].astype(np.float64) @ H
+                den = np.linalg.norm(t["M"]) + np.linalg.norm(AH)
                 assert np.linalg.norm(Gg - t["G"]) / den <= 1e-5
+                assert_elementwise(Gg, t["G"], 1e-5, np.abs(t["M"]).max(axis=1) + np.abs(AH).max(axis=1))
                 zg = g.tap("ZPREV", n)
                 zs = max(np.abs(t["Z"]).max(), 1e-30)
                 # 1e-5 of max |z|, widened per element by the FP32 evaluation bound of Eq. 11-12, 20
@@ -119,6 +145,7 @@ def test_mttkrp_gram_and_mode_step_replay(case):
                 An = g.factor(n)
                 assert (An >= 0).all()
                 assert relerr(An, o.A[n]) <= 1e-5
+                assert_rowwise(An, o.A[n], 1e-5, np.linalg.norm(F[n].astype(np.float64), axis=1))
                 assert nsel == int(mask.sum())
                 stn = g.tap("STATE", n)
                 assert stn[1] == 0.0
@@ -219,6 +246,16 @@ def test_graph_iterate_equals_mode_steps_and_is_deterministic():
         assert a.fit() == b.fit()
 
 
+def resync(o, g, n_modes):
+    """Give the oracle the GPU's state: factors, z^{k-1}, ti^{k-1} and first-visit flags."""
+    o.A = [f.astype(np.float64) for f in g.factors()]
+    for n in range(n_modes):
+        o.Zprev[n] = g.tap("ZPREV", n).astype(np.float64)
+        st = g.tap("STATE", n)
+        o.tiprev[n] = st[0]
+        o.first[n] = st[1] != 0
+
+
 def test_bf16_gather_mode():
     dims, nnz, dist, s, R = CASES[1]
     idx, vals, init = make_case(dims, nnz, dist, s, R)
@@ -240,15 +277,67 @@ def test_bf16_gather_mode():
                 ob.first[n] = st[1] != 0
                 ob.mode_step(n, mask=g.tap("MASK", n, last_mode=n).astype(bool))
                 assert relerr(g.tap("M", n), ob.last["M"]) <= 1e-5
+                Mref = ob.last["M"]
+                rowmax = np.abs(Mref).max(axis=1, keepdims=True)
+                assert (np.abs(g.tap("M", n) - Mref) <= 1e-5 * (np.abs(Mref) + rowmax)).all()
                 assert relerr(g.factor(n), ob.A[n]) <= 1e-5
+    # 30 iterations, each one checked against an iteration of the oracle's BF16-gather definition
+    # from the GPU's state at its start (selection replayed): fit within 1e-3 (the stated bound;
+    # observed ~1e-7), factors within 1e-4.
     with S.SaCD(dims, idx, vals, R, init, precision=S.SACD_BF16_GATHER) as g:
-        o = O.SaCDOracle(dims, idx, vals, init)
+        g.set_debug(True)
+        ob = O.SaCDOracle(dims, idx, vals, init, gather="bf16")
+        worst = 0.0
+        for it in range(30):
+            resync(ob, g, 3)
+            for n in range(3):
+                g.mode_step(n, want_count=False)
+                ob.mode_step(n, mask=g.tap("MASK", n, last_mode=n).astype(bool))
+            worst = max(worst, abs(g.fit()[1] - ob.fit()[1]))
+            for n in range(3):
+                assert relerr(g.factor(n), ob.A[n]) <= 1e-4
+        print(f"bf16 iteration-by-iteration: worst |dfit| {worst:.3e}")
+        assert worst <= 1e-3
+    # The free trajectory (each side its own selection, 30 iterations). With identical selections
+    # an FP32-gather run drifts from the oracle by up to 4e-4 of each factor's largest entry over
+    # 30 iterations (FP32 step errors accumulating) while its fit agrees to 4e-7; with BF16 gathers
+    # that drift flips BF16 codes (a gathered value moves by one BF16 ulp, 2^-8 relative, whenever
+    # the two states straddle a rounding boundary: 6 codes in the first iteration, 1,807 by the
+    # sixth), and Eq. 24/27 are discontinuous, so BF16 trajectories of equal definition separate:
+    # two FP64 oracle runs of this case that differ only in rounding the factors to FP32 after
+    # each step end 1.1e-3 to 2.5e-3 apart. The GPU's free trajectory is held to twice that spread.
+    with S.SaCD(dims, idx, vals, R, init, precision=S.SACD_BF16_GATHER) as g:
+        ob = O.SaCDOracle(dims, idx, vals, init, gather="bf16")
         g.iterate(30)
-        o.iterate(30)
-        # BF16 rounding of the gathered rows flips selections (Eq. 24/27 are discontinuous),
-        # so whole trajectories drift: an FP64 emulation that only rounds the gathered
-        # factors moves the fit of this case by 1.7e-3 after 10 and 0.9e-3 after 30 iterations.
-        assert abs(g.fit()[1] - o.fit()[1]) <= 5e-3
+        ob.iterate(30)
+        dfit = abs(g.fit()[1] - ob.fit()[1])
+        print(f"bf16 free trajectory: |dfit| {dfit:.3e}")
+        assert dfit <= 5e-3
+
+
+@pytest.mark.parametrize("prec", [S.SACD_FP32, S.SACD_BF16_GATHER], ids=["fp32", "bf16"])
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3]], ids=ids)
+def test_fit_at_identical_factors(case, prec):
+    """sacd_fit is the objective (Eq. 6-8) of the factors the context returns, in both
+    precisions: after 5 iterations, against the oracle's FP64 objective of exactly those FP32
+    factors. Bound: the FP32 MTTKRP behind <X, model> carries a rounding error of about
+    sqrt(chain) * 2^-24 relative (chains of a few hundred partial sums: ~1e-6); the FP64 Grams
+    1e-10. A fit formed from BF16-gathered rows is off by ~3e-4 of <X, model>."""
+    dims, nnz, dist, s, R = case
+    idx, vals, init = make_case(dims, nnz, dist, s, R)
+    cidx, cvals = O.coalesce(dims, idx, vals)
+    with S.SaCD(dims, idx, vals, R, init, precision=prec) as g:
+        for k in range(2):
+            g.iterate(1 if k == 0 else 4)
+            F = g.factors()
+            obj, fit = g.fit()
+            nx = O.norm_x_sq(cvals)
+            inner = O.inner_x_model(cidx, cvals, F)
+            mn = O.model_norm_sq(F)
+            ref = nx - 2.0 * inner + mn
+            assert np.isfinite(obj)
+            assert abs(obj - ref) <= 2.0 * 2e-6 * abs(inner) + 1e-9 * mn + 1e-12 * nx, (obj, ref)
+            assert fit == pytest.approx(O.fit_from_objective(obj, nx), rel=1e-12, abs=1e-15)
 
 
 @pytest.mark.parametrize("prec", [S.SACD_FP32, S.SACD_BF16_GATHER], ids=["fp32", "bf16"])
@@ -338,28 +427,131 @@ def test_device_inputs_from_torch():
             np.testing.assert_array_equal(a.factor(n), b.factor(n))
 
 
-def test_full_size_zipf_workload_sampled_rows():
-    """The 50,000 x 20,000 x 500, 5M-nonzero Zipf(1.1) rank-32 workload, in the launch
-    configuration the benchmark uses: MTTKRP rows checked against the oracle row by row on a
-    sample (the heaviest rows plus random ones), and the step's invariants at full size."""
+def check_step_rows(g, n, F, zprev, st, mask, rows, M_rows, bf16=False):
+    """One GPU mode step of mode n checked on the given rows against the oracle's definitions,
+    from the same factors and importance state with the GPU's selection: M (the oracle's MTTKRP of
+    those rows, given), G, z, the selection's validity (free disagreements only at the decision
+    boundary) and the updated rows of A."""
+    H = O.hadamard_of_grams([f.astype(np.float64) for f in F], n)
+    L = O.lipschitz(H)
+    h = O.curvatures(H)
+    A = F[n].astype(np.float64)[rows]
+    G = A @ H - M_rows
+    Sd = O.projected_delta(A, G, h[None, :])
+    Z = O.importance(G, Sd, L)
+    t = dict(G=G, H=H, L=L)
+    Mg = g.tap("M", n)[rows]
+    assert relerr(Mg, M_rows) <= 1e-5
+    assert_elementwise(Mg, M_rows, 1e-5)
+    Gg = g.tap("G", n, last_mode=n)[rows]
+    AH = A @ H
+    assert_elementwise(Gg, G, 1e-5, np.abs(M_rows).max(axis=1) + np.abs(AH).max(axis=1))
+    zg = g.tap("ZPREV", n)[rows]
+    zs = max(np.abs(Z).max(), 1e-30)
+    assert (np.abs(zg - Z) <= 1e-5 * zs + z_fp32_bound(A, t)).all()
+    m = mask[rows]
+    first = st[1] != 0
+    branch = g.tap("STATE", n)[3]
+    zp = zprev[rows].astype(np.float64)
+    if first:
+        own, sp = Z > 0, Z
+    elif branch == 2.0:
+        own, sp = (zp - Z) > 0, zp - Z
+    else:
+        own, sp = (Z - zp) > 0, Z - zp
+    dis = own != m
+    assert (np.abs(sp[dis]) <= 1e-5 * zs + z_fp32_bound(A, t)[dis]).all()
+    Anew, _ = O.update_rows(A, G, H, m, "column_gs", h)
+    An = g.factor(n)[rows]
+    assert (An >= 0).all()
+    assert_rowwise(An, Anew, 1e-5, np.linalg.norm(A, axis=1))
+
+
+def heavy_and_random_rows(idx_n, dim, k_heavy, k_rand, seed):
+    counts = np.bincount(idx_n, minlength=dim)
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([np.argsort(counts)[-k_heavy:], rng.integers(0, dim, k_rand)]))
+
+
+def test_full_size_zipf_workload_every_element():
+    """The 50,000 x 20,000 x 500, 5M-nonzero Zipf(1.1) rank-32 workload, in the launch configuration
+    the benchmark uses: one iteration (all three modes), every element of M, G, z and A and the
+    selection against the oracle from the same factors with the GPU's selection, plus the MTTKRP
+    rows of the heaviest (split) rows element by element."""
     w = synth.WORKLOADS["zipf1.1-50000x20000x500-5M-r32"]
     idx, vals, init = synth.make_workload(w)
     with S.SaCD(w.dims, idx, vals, w.rank, init) as g:
         assert g.info["nnz"] == w.nnz
-        rng = np.random.default_rng(0)
+        assert max(g.info["split_rows"][:3]) > 0
+        g.set_debug(True)
         for n in range(3):
             F = g.factors()
-            g.mode_step(n)
-            M = g.tap("M", n)
-            counts = np.bincount(idx[n], minlength=w.dims[n])
-            rows = np.unique(np.concatenate([np.argsort(counts)[-16:], rng.integers(0, w.dims[n], 48)]))
+            zprev = g.tap("ZPREV", n)
+            st = g.tap("STATE", n)
+            g.mode_step(n, want_count=False)
+            mask = g.tap("MASK", n, last_mode=n).astype(bool)
+            M = O.mttkrp(list(w.dims), idx, vals, F, n)
+            check_step_rows(g, n, F, zprev, st, mask, np.arange(w.dims[n]), M)
+        assert np.isfinite(g.fit()[0])
+
+
+def test_full_size_bf16_4mode_workload_sampled_rows():
+    """The 200,000 x 100,000 x 10,000 x 200, 50M-nonzero Zipf(1.2) rank-64 BF16-gather workload in
+    the benchmark's launch configuration: one iteration (all four modes), M, G, z, the selection
+    and A on sampled rows (the heaviest rows, split across many tiles, plus random ones) against the
+    oracle's BF16-gather definition from the same factors with the GPU's selection; M also loosely
+    against FP32 gathers."""
+    w = synth.WORKLOADS["zipf1.2-200000x100000x10000x200-50M-r64-bf16"]
+    idx, vals, init = synth.make_workload(w)
+    with S.SaCD(w.dims, idx, vals, w.rank, init, precision=S.SACD_BF16_GATHER) as g:
+        assert g.info["nnz"] == w.nnz
+        g.set_debug(True)
+        for n in range(4):
+            F = g.factors()
+            zprev = g.tap("ZPREV", n)
+            st = g.tap("STATE", n)
+            g.mode_step(n, want_count=False)
+            mask = g.tap("MASK", n, last_mode=n).astype(bool)
+            rows = heavy_and_random_rows(idx[n], w.dims[n], 8, 24, n)
             keep = np.isin(idx[n], rows)
-            sub = idx[:, keep]
-            Mref = O.mttkrp(list(w.dims), sub, vals[keep], F, n)[rows]
-            assert relerr(M[rows], Mref) <= 1e-5
-            assert (g.factor(n) >= 0).all()
-        obj, fit = g.fit()
-        assert np.isfinite(obj)
+            Fb = [O.round_bf16(f) for f in F]
+            ref_b = O.mttkrp(list(w.dims), idx[:, keep], vals[keep], Fb, n)[rows]
+            ref = O.mttkrp(list(w.dims), idx[:, keep], vals[keep], F, n)[rows]
+            assert relerr(g.tap("M", n)[rows], ref) <= 1e-2
+            check_step_rows(g, n, F, zprev, st, mask, rows, ref_b, bf16=True)
+        assert np.isfinite(g.fit()[0])
+
+
+@pytest.mark.slow
+def test_full_size_zipf_workload_50_iterations():
+    """The 5M-nonzero workload's own iteration count, 50 iterations (about five minutes of oracle
+    time on the host). (1) Iterations 1, 10, 25 and 50, each run by the oracle from the GPU's state
+    at its start with the GPU's selection, end within 1e-4 of the GPU's fit. (2) The free
+    trajectories end within 2e-3: on this workload the selection (Eq. 24/27, discontinuous)
+    amplifies FP32-sized gradient errors; an FP64 oracle whose gradient carries noise of 4 FP32
+    ulps of |A||H| + |M| drifts from the exact oracle by 1.0e-2 after 10, 6.4e-4 after 20, 3.3e-4
+    after 30 and 5.0e-4 after 40 iterations (rounding only its factors to FP32 after each step:
+    at most 1.9e-5), so no FP32 implementation meets 1e-4 on the free 50-iteration trajectory."""
+    w = synth.WORKLOADS["zipf1.1-50000x20000x500-5M-r32"]
+    idx, vals, init = synth.make_workload(w)
+    o = O.SaCDOracle(w.dims, idx, vals, init)
+    with S.SaCD(w.dims, idx, vals, w.rank, init) as g:
+        g.set_debug(True)
+        for it in range(1, w.iters + 1):
+            if it in (1, 10, 25, 50):
+                resync(o, g, 3)
+                for n in range(3):
+                    g.mode_step(n, want_count=False)
+                    o.mode_step(n, mask=g.tap("MASK", n, last_mode=n).astype(bool))
+                assert abs(g.fit()[1] - o.fit()[1]) <= 1e-4
+            else:
+                g.iterate(1)
+        fit = g.fit()[1]
+        assert all((A >= 0).all() for A in g.factors())
+    o = O.SaCDOracle(w.dims, idx, vals, init)
+    o.iterate(w.iters)
+    print(f"5M workload, 50 free iterations: |dfit| {abs(fit - o.fit()[1]):.3e}")
+    assert abs(fit - o.fit()[1]) <= 2e-3, (fit, o.fit()[1])
 
 
 @pytest.mark.parametrize("sub", [4, 16, 64, 256])
@@ -379,26 +571,3 @@ def test_retiling_keeps_mttkrp_and_step(sub):
         assert all((A >= 0).all() for A in g.factors())
 
 
-def test_full_size_bf16_4mode_workload_sampled_rows():
-    """The 200,000 x 100,000 x 10,000 x 200, 50M-nonzero Zipf(1.2) rank-64 BF16-gather workload in
-    the benchmark's launch configuration: MTTKRP rows checked on a sample (the heaviest rows plus
-    random ones) against the oracle's BF16-gather definition and, loosely, against FP32 gathers."""
-    w = synth.WORKLOADS["zipf1.2-200000x100000x10000x200-50M-r64-bf16"]
-    idx, vals, init = synth.make_workload(w)
-    with S.SaCD(w.dims, idx, vals, w.rank, init, precision=S.SACD_BF16_GATHER) as g:
-        assert g.info["nnz"] == w.nnz
-        rng = np.random.default_rng(1)
-        for n in range(4):
-            F = g.factors()
-            g.mode_step(n, want_count=False)
-            M = g.tap("M", n)
-            counts = np.bincount(idx[n], minlength=w.dims[n])
-            rows = np.unique(np.concatenate([np.argsort(counts)[-8:], rng.integers(0, w.dims[n], 24)]))
-            keep = np.isin(idx[n], rows)
-            Fb = [O.round_bf16(f) for f in F]
-            ref_b = O.mttkrp(list(w.dims), idx[:, keep], vals[keep], Fb, n)[rows]
-            ref = O.mttkrp(list(w.dims), idx[:, keep], vals[keep], F, n)[rows]
-            assert relerr(M[rows], ref_b) <= 1e-5
-            assert relerr(M[rows], ref) <= 1e-2
-            assert (g.factor(n) >= 0).all()
-        assert np.isfinite(g.fit()[0])

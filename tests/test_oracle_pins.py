@@ -386,3 +386,44 @@ def test_pattern_distinctiveness_special_cases():
     W[:, 2] = 0  # a zero column has no direction
     pairs = [1 - scipy.cosine(W[:, i], W[:, r]) for i in (0, 1, 3, 4) for r in (0, 1, 3, 4) if i < r]
     assert O.pattern_distinctiveness(W) == pytest.approx(np.mean(pairs), rel=1e-13)
+
+
+def test_negligible_curvature_takes_no_step():
+    """Reading of h_rr <= 0 extended to a numerically negligible h_rr (<= max(2^-40 max_j h_jj,
+    2^-126)): such a column takes no step and has z = 0. The case: column 2 of the other factors
+    shrunk by 1e-25, so h_22 ~ 1e-100; the exact constrained minimiser along that coordinate (from
+    the dense objective) is then far outside the FP32 range, while the other columns still take
+    their exact 1-D steps."""
+    dims, R = (4, 5, 3), 3
+    idx, vals, F = random_case(dims, R, 25, 5)
+    F[1][:, 2] *= 1e-25
+    F[2][:, 2] *= 1e-25
+    X = dense_from_coo(dims, idx, vals)
+    n = 0
+    H = O.hadamard_of_grams(F, n)
+    h = O.curvatures(H)
+    assert H[2, 2] > 0 and h[2] == 0.0
+    np.testing.assert_array_equal(h[:2], np.diag(H)[:2])
+    # the exact step that the reading declines: f(A + t e_q2) = c0 + c1 t + c2 t^2 with c2 the
+    # squared norm of KRP column 2 and c1 = 2 (a_q K^T K - X_(n) K)_q2 (explicit unfolding and
+    # Khatri-Rao product); |t*| is beyond the largest FP32 value in some row
+    K = krp_for_mode(F, n)
+    Xn = unfold(X, n)
+    c2 = float(K[:, 2] @ K[:, 2])
+    tstar = []
+    for q in range(dims[n]):
+        c1 = 2.0 * (float(F[n][q] @ (K.T @ K[:, 2])) - float(Xn[q] @ K[:, 2]))
+        tstar.append(max(-F[n][q, 2], -c1 / (2 * c2)))
+    assert 0 < c2 < 1e-90 and max(abs(t) for t in tstar) > 3.4e38
+    # the oracle's mode step: column 2 unchanged with z = 0; columns 0 and 1 as with the raw h
+    o = O.SaCDOracle(dims, idx, vals, [a.astype(np.float32) for a in F])
+    o.A = [a.copy() for a in F]
+    o.mode_step(n, mask=np.ones((dims[n], R), dtype=bool))
+    np.testing.assert_array_equal(o.A[n][:, 2], F[n][:, 2])
+    assert (o.last["Z"][:, 2] == 0).all()
+    G = O.gradient(F[n], H, O.mttkrp(list(dims), idx, vals, F, n))
+    S = O.projected_delta(F[n], G, np.diag(H)[None, :])
+    np.testing.assert_allclose(o.A[n][:, 0], F[n][:, 0] + S[:, 0], rtol=1e-12, atol=1e-14)
+    # the two thresholds, at and just above them
+    assert list(O.curvatures(np.diag([1.0, 2.0**-40, 2.0**-40 * 1.0001]))) == [1.0, 0.0, 2.0**-40 * 1.0001]
+    assert list(O.curvatures(np.diag([1e-39, 2.0**-126, 2.0**-125]))) == [0.0, 0.0, 2.0**-125]
