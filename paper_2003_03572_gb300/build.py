@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsacd.so")
-SOURCES = ["prep.cu", "mttkrp.cu", "update.cu", "selupd.cu", "sacd.cu", "noalloc.cu"]
+SOURCES = ["prep.cu", "mttkrp.cu", "update.cu", "selupd.cu", "gram_tc.cu", "sacd.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -35,6 +35,11 @@ void launch_pass2(const StepDesc* d_descs, const int64_t* d_base, int njobs, int
                   cudaStream_t st);
 void launch_gram(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
                  cudaStream_t st);
+// Gram on the tensor cores (gram_tc.cu) for padded ranks 32 and 64: exact BF16 split, FP64 result
+bool gram_on_tensor_cores(int Rp);
+int gram_tc_blocks(int64_t I);  // blocks (per-block partials) of one Gram on the tensor cores
+void launch_gram_tc(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+                    cudaStream_t st);
 int gram_reduce_blocks(int Rp);
 void launch_gram_reduce(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks,
                         cudaStream_t st);

@@ -806,7 +806,7 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     md.p2_blocks = (I + RB2 - 1) / RB2;
     md.sel_rt = selupd_choose_rt(I, Rp);
     md.sel_chunks = selupd_chunks(I, Rp, md.sel_rt);
-    md.gram_blocks = std::min<int64_t>((I + CH - 1) / CH, 4 * 152);
+    md.gram_blocks = gram_on_tensor_cores(Rp) ? gram_tc_blocks(I) : std::min<int64_t>((I + CH - 1) / CH, 4 * 152);
     p1_max = std::max(p1_max, md.p1_blocks);
     gb_max = std::max(gb_max, md.gram_blocks);
     TRY(dalloc(c, &md.A, (size_t)I * Rp));

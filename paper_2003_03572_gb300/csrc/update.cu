@@ -588,6 +588,10 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const StepDesc* __rest
 void launch_gram(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
                  cudaStream_t st) {
   if (total_blocks <= 0) return;
+  if (gram_on_tensor_cores(Rp)) {
+    launch_gram_tc(d_descs, d_base, njobs, total_blocks, Rp, st);
+    return;
+  }
   if (Rp <= 16)
     gram_kernel<1><<<(unsigned)total_blocks, 256, 0, st>>>(d_descs, d_base, njobs);
   else if (Rp == 32)

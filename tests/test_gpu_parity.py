@@ -3,7 +3,9 @@
 Tolerances (written here, from the stated targets):
 * CSF sort, repeat summation: bit-exact.
 * MTTKRP: relative Frobenius error <= 1e-5 (FP32 gathers), <= 1e-2 (BF16 gathers).
-* Gram: <= 1e-10 relative (compensated FP32 products/sums, FP64 result).
+* Gram: <= 1e-10 relative (compensated FP32 products/sums at ranks up to 16, an exact BF16 split
+  on the tensor cores at padded ranks 32 and 64; FP64 result), and every entry within
+  1e-12 sqrt(G_jj G_kk).
 * G: <= 1e-5 relative to ||M||_F + ||A H||_F (avoids cancellation blow-up).
 * one mode step from identical factors, with the selection fixed on both sides (the oracle
   replays the GPU's mask): factor after the step <= 1e-5 relative; z <= 1e-5 of max |z|.
@@ -162,6 +164,31 @@ def test_mttkrp_gram_and_mode_step_replay(case):
                     ti_close = abs(t["ti"] - t["tiprev"]) <= 1e-6 * np.abs(t["Z"]).sum()
                     zb = z_fp32_bound(F[n], t)
                     assert ti_close or (np.abs(sp[dis]) <= 1e-5 * zs + zb[dis]).all()
+
+
+@pytest.mark.parametrize("R", [64, 32, 24, 40], ids=lambda r: f"r{r}")
+def test_gram_on_tensor_cores_many_blocks(R):
+    """Initial Grams of a 300,000-row mode: every block spans several read-back periods of the
+    tensor-core Gram, the last block is ragged, and the factor has a column scaled by 2^-30, rows
+    a million times larger than the rest in another column, and an all-zero column."""
+    dims = (300_000, 300, 40)
+    idx, vals = synth.sparse_tensor(dims, 20_000, dist="zipf", zipf_s=1.1, seed=3)
+    rng = np.random.default_rng(4)
+    init = synth.init_factors(dims, R, 4)
+    A0 = (rng.random((dims[0], R)) ** 3).astype(np.float32)
+    A0[:, 1] *= np.float32(2.0**-30)
+    A0[::997, 2] *= np.float32(1e6)
+    A0[:, R - 1] = 0.0
+    init[0] = A0
+    with S.SaCD(dims, idx, vals, R, init) as g:
+        for n in range(len(dims)):
+            ref = O.gram(init[n])
+            got = g.tap("GRAM", n)
+            assert np.isfinite(got).all()
+            assert relerr(got, ref) <= 1e-10
+            d = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+            assert (np.abs(got - ref) <= 1e-12 * d + 1e-300).all()
+            assert np.array_equal(got, got.T)
 
 
 @pytest.mark.parametrize("lnorm,fixup", [(S.SACD_LNORM_SPECTRAL, 0), (S.SACD_LNORM_GCD, 0), (0, S.SACD_FIXUP_LEMMA2)])
