@@ -3,41 +3,46 @@
 //
 // Split. Block b takes a contiguous range of rows. Pass 1 streams the range once for the column
 // maxima; e_j is the exponent of column j's largest magnitude over the range, so every scaled value
-// t = a 2^-e_j lies in (-1, 1). Pass 2 cuts t into kTcSlices slices of 7 bits: s_1 = trunc(128 t),
-// t <- 128 t - s_1, and so on. Every s is an integer of magnitude at most 127, exact in BF16, and
-// a_ij = 2^e_j sum_p s_p,ij 2^-7p up to 2^(e_j - 49). Then
+// t = a 2^-e_j lies in (-1, 1). Pass 2 cuts t into kTcSlices signed base-128 digits:
+// s_1 = rint(128 t), t <- 128 t - s_1 (now in [-1/2, 1/2]), and so on. |s_1| <= 128 and
+// |s_p| <= 64 after it; all are integers exact in BF16, and a_ij = 2^e_j sum_p s_p,ij 2^-7p up to
+// 2^(e_j - 50). Then
 // (A^T A)_jk = 2^(e_j + e_k) sum_d 2^-7d D_d,jk with D_d = sum over slice pairs p + q = d of
 // S_p^T S_q; the pairs with d <= 8 are formed (the next diagonal weighs 2^-56 of the first).
 //
 // Products. One tcgen05.mma (kind::f16: BF16 operands, FP32 accumulator in tensor memory) forms a
-// 128 x Rp x 16 product from shared-memory operands in the canonical K-major layout without
+// 128 x 128 x 16 product from shared-memory operands in the canonical K-major layout without
 // swizzle (core matrices of 8 rows x 16 bytes; LBO = 128 B between core matrices along K, SBO
-// between those along M or N). The 128-row A operand stacks G = 128 / Rp consecutive slices
-// S_p .. S_p+G-1 (slices are stored back to back, zero past the seventh), so accumulator T_t, fed
-// the pairs (p, q) with p in {1, 1+G, 1+2G, ..} and p + q = t, holds in its quarter r the pairs
-// (p + r, q): diagonal t + r. Every pair with d <= 8 lands in exactly one (T_t, quarter) and no
-// tensor-memory lane is wasted.
+// between those along M or N). Both operands stack G = 128 / Rp consecutive slices (slices are
+// stored back to back, zero past the seventh): the product of stacks p and q holds in its block
+// (r, c) the slice pair (p + r, q + c), diagonal p + q + r + c. The stacks start at
+// p, q in {1, 1+G, 1+2G, ..}; the products with p + q <= 8 cover every pair with d <= 8 exactly
+// once (10 products at Rp = 64, 3 at Rp = 32), and those with equal p + q = t share accumulator
+// T_t. Small products (N = Rp) would be bound by the operand reads from shared memory; at
+// 128 x 128 the reads and the arithmetic take about the same time.
 //
-// Exactness. Slice products are exact in FP32 and their sums are integers. The accumulators
-// T_2 .. T_5 hold at most two pairs per quarter; they are read back (tcgen05.ld) and restarted
-// every kTcPeriod rows, few enough that their sums stay below 2^24 (2 * 512 * 127^2 < 2^24 at
-// Rp = 64, 1 * 1024 * 127^2 at Rp = 32), so they are exact. T_6 .. T_8 (diagonals >= 6, weight
-// <= 2^-28 of the first) run over the whole range and are read once; their FP32 rounding moves
-// the result by less than 2^-52 per product step. Each thread owns one tensor-memory lane (one
-// Gram row of one quarter) and half of its columns, and keeps the scaled sums as unevaluated FP32
-// pairs (hi, lo) built with error-free two_sum (Knuth), renormalised after every read-back. At
-// the end the quarters are summed the same way and each entry becomes one FP64 number,
-// 2^(e_j + e_k) (hi + lo), assembled from the FP32 bit fields (one FP64 add per entry: FP64
-// arithmetic is scarce on this part). The per-block partials are summed by gram_reduce_kernel, as
-// for the FP32-pipe Gram.
+// Exactness. Slice products are exact in FP32 and their sums are integers. Every accumulator is
+// read back (tcgen05.ld) and restarted after each period of kTcPeriod = 1024 rows. Each block of
+// an accumulator with d <= 5 holds pairs whose digit products add up to at most 2^14 per row
+// (the first digits are at most 128, the others at most 64), so over a period its sums stay
+// within 2^24 and are exact. Blocks with d >= 6 may round: at most 64 accumulation steps of at
+// most one unit each per period, weighted 2^-7d <= 2^-42, i.e. below 2^-36 2^(e_j + e_k) per
+// period. Each worker thread owns one tensor-memory lane (row j of one block row r) and half of
+// the columns, that is the Gram entries (j, k) of one or two block columns c, and keeps the
+// scaled sums as unevaluated FP32 pairs (hi, lo) built with error-free two_sum (Knuth),
+// renormalised after every read-back. At the end the pairs of all blocks are summed the same way
+// and each entry becomes one FP64 number, 2^(e_j + e_k) (hi + lo), assembled from the FP32 bit
+// fields (one FP64 add per entry: FP64 arithmetic is scarce on this part). The per-block partials
+// are summed by gram_reduce_kernel, as for the FP32-pipe Gram.
 //
-// Pipeline. Pass 1 keeps up to kNst1 bulk copies (cp.async.bulk, completion counted on an
-// mbarrier) in flight over all of shared memory. Pass 2 double-buffers both the raw FP32 rows and
-// the slices: while the tensor cores multiply fill f, the block slices fill f + 1 and the copy of
-// fill f + 2 is in flight. One elected thread issues the copies and the MMAs and commits the MMAs
-// to an mbarrier per slice buffer. Every wait is bounded by a clock64() budget; on expiry the
-// block stops issuing work, waits (again bounded) for what it has in flight, writes NaN as its
-// partial (so the step's result is visibly wrong), and frees its tensor memory.
+// Pipeline. Eight worker warps and one issuing warp. Pass 1 keeps up to NST1 bulk copies
+// (cp.async.bulk, completion counted on an mbarrier) in flight over all of shared memory. In pass
+// 2 the issuing warp's elected thread keeps kTcNraw copies of raw FP32 rows in flight and issues
+// each fill's MMAs once the workers have sliced it (an mbarrier per slice buffer), committing them
+// to another mbarrier per buffer; meanwhile the workers slice the next fill. Every wait is bounded
+// by a clock64() budget; on expiry the block stops issuing work, waits (again bounded) for what it
+// has in flight, writes NaN as its partial (so the step's result is visibly wrong), and frees its
+// tensor memory.
 #include <cstdint>
 
 #include "common.cuh"
@@ -47,32 +52,37 @@ namespace sacd {
 
 namespace {
 
-constexpr int kTcSlices = 7;      // slices of 7 bits below the column scale
+constexpr int kTcSlices = 7;      // base-128 digits below the column scale
 constexpr int kTcKB = 64;         // rows per fill (4 MMA k-steps of 16)
-constexpr int kTcThreads = 256;
+constexpr int kTcWorkers = 256;   // 8 worker warps: slicing, read-backs, the final sums
+constexpr int kTcThreads = kTcWorkers + 32;  // and the issuing warp
 constexpr int kTcMinRows = 512;   // fewest rows a block is given
+constexpr int kTcPeriod = 1024;   // rows between read-backs of the accumulators
+constexpr int kTcNraw = 4;        // raw fills in flight in pass 2
+constexpr int kTcN = 128;         // MMA shape 128 x 128 x 16
 constexpr long long kTcWaitCycles = 1LL << 31;
 
 template <int NR>
 struct TcShape {
-  static constexpr int G = 128 / NR;                          // slices stacked in one A operand
-  static constexpr int NSLICE = kTcSlices + G - 1;            // stacked operands reach slice 7+G-1
+  static constexpr int G = kTcN / NR;                         // slices stacked in one operand
+  static constexpr int NSLICE = 8;                            // the last stack reaches slice 8
   static constexpr int SBO = (kTcKB / 8) * 128;               // bytes between core matrices along M / N
   static constexpr int SLICE_BYTES = NR * kTcKB * 2;          // one slice: NR rows x kTcKB BF16
   static constexpr int SLICEBUF = NSLICE * SLICE_BYTES;       // one fill's slices
   static constexpr int STAGE = kTcKB * NR * 4;                // one fill's raw FP32 rows
-  static constexpr int REGION = 2 * SLICEBUF + 2 * STAGE;     // slices + raw rows
+  static constexpr int REGION = 2 * SLICEBUF + kTcNraw * STAGE;
   static constexpr int NST1 = REGION / STAGE;                 // pass-1 copies in flight
-  static constexpr int PERIOD_FILLS = (NR == 64 ? 512 : 1024) / kTcKB;  // fills between read-backs of T_2..T_5
-  static constexpr int NACC = 7;                              // accumulators T_2 .. T_8
-  static constexpr int TALLOC = NACC * NR <= 256 ? 256 : 512; // tensor-memory columns
-  static constexpr int NCOL = NR / 2;                         // Gram columns a thread owns
-  static constexpr int CSTRIDE = NR + 1;                      // padded row of the quarter sums (float2)
-  static constexpr int NBAR = NST1 + 4;
-  static constexpr size_t SMEM = (size_t)REGION + 2 * NR * sizeof(int) + NBAR * sizeof(uint64_t) + 16;
+  static constexpr int PERIOD_FILLS = kTcPeriod / kTcKB;
+  static constexpr int NACC = (8 - 2) / G + 1;                // accumulators T_2, T_2+G, .. T_8
+  static constexpr int TALLOC = NACC * kTcN;                  // tensor-memory columns (512 or 256)
+  static constexpr int NQ = 2 * G;                            // (block row, column half) groups
+  static constexpr int CSTRIDE = NR + 1;                      // padded row of the group sums (float2)
+  static constexpr int NBAR = NST1 + kTcNraw + 4;             // pass 1, raw, done x2, ready x2
+  static constexpr size_t SMEM = (size_t)REGION + 2 * NR * sizeof(int) + NBAR * sizeof(uint64_t) + 64;
   static_assert(REGION % STAGE == 0, "stages tile the region");
-  static_assert((size_t)G * NR * CSTRIDE * 8 <= (size_t)REGION, "quarter sums fit the region");
-  static_assert(NST1 >= 2, "at least two stages");
+  static_assert((size_t)NQ * NR * CSTRIDE * 8 <= (size_t)REGION, "group sums fit the region");
+  static_assert(TALLOC == 256 || TALLOC == 512, "tensor-memory allocation");
+  static_assert((1 + G * ((7 - 1) / G)) + G - 1 <= NSLICE, "stacks stay inside the slice buffer");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -178,6 +188,21 @@ __device__ __forceinline__ void bar_drain(uint32_t addr, BarTrack& t) {
 
 }  // namespace
 
+// worker-only barrier (named barrier 1, the 8 worker warps) and its AND-reduction
+__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kTcWorkers) : "memory"); }
+__device__ __forceinline__ bool workers_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kTcWorkers)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
 template <int NR>
 __global__ void __launch_bounds__(kTcThreads, 1)
     gram_tc_kernel(const StepDesc* __restrict__ descs, const int64_t* __restrict__ base, int njobs) {
@@ -196,22 +221,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int nf = (int)((r1 - r0 + kTcKB - 1) / kTcKB);
 
   unsigned char* slices = tsm;                      // 2 fills of slices
-  unsigned char* raw = tsm + 2 * TS::SLICEBUF;      // 2 fills of raw rows
+  unsigned char* raw = tsm + 2 * TS::SLICEBUF;      // kTcNraw fills of raw rows
   unsigned* cmax = reinterpret_cast<unsigned*>(tsm + TS::REGION);
   int* cexp = reinterpret_cast<int*>(cmax + NR);
   uint64_t* bars = reinterpret_cast<uint64_t*>(cexp + NR);  // 8-byte aligned: REGION and 2 NR ints are
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + TS::NBAR);
-  const uint32_t bar1 = smem_u32(bars), bar2 = smem_u32(bars + TS::NST1), barm = smem_u32(bars + TS::NST1 + 2);
+  uint32_t* misc = reinterpret_cast<uint32_t*>(bars + TS::NBAR);  // tslot, abort, issued counts
+  volatile uint32_t* abort_flag = misc + 1;
+  uint32_t* iss = misc + 2;  // [0, kTcNraw): raw copies per stage; [kTcNraw, +2): commits per buffer
+  const uint32_t bar1 = smem_u32(bars), bar2 = bar1 + 8 * TS::NST1, barm = bar2 + 8 * kTcNraw, bary = barm + 16;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool worker = warp < kTcWorkers / 32;
 
   if (tid < NR) cmax[tid] = 0u;
   if (tid == 0) {
-    for (int i = 0; i < TS::NBAR; ++i) mbar_init(smem_u32(bars + i), 1);
+    for (int i = 0; i < TS::NST1 + kTcNraw + 2; ++i) mbar_init(bar1 + 8 * i, 1);
+    for (int i = 0; i < 2; ++i) mbar_init(bary + 8 * i, kTcWorkers);
+    *abort_flag = 0u;
+    for (int i = 0; i < kTcNraw + 2; ++i) iss[i] = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+  if (warp == kTcWorkers / 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(misc)),
                  "r"(TS::TALLOC)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -219,106 +250,164 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tbase = *tslot;
+  const uint32_t tbase = misc[0];
   bool ok = ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) && dp->Rp == NR;  // bulk copies need 16-byte rows
   auto fill_bytes = [&](int f) { return (uint32_t)(min((int64_t)kTcKB, r1 - r0 - (int64_t)f * kTcKB) * NR * 4); };
   auto fill_src = [&](int f) { return A + (r0 + (int64_t)f * kTcKB) * NR; };
 
-  // ---- pass 1: column maxima over the block's rows, kNst1 copies in flight
-  BarTrack t1[TS::NST1];
-  if (ok) {
-    if (tid == 0)
-      for (int f = 0; f < min(nf, TS::NST1); ++f)
-        bulk_load(smem_u32(tsm + f * TS::STAGE), fill_src(f), fill_bytes(f), bar1 + 8 * f);
-    for (int f = 0; f < min(nf, TS::NST1); ++f) t1[f].issued = 1;
-    unsigned mx[4] = {0u, 0u, 0u, 0u};  // bits of |x|: they order as |x|, NaN above +inf
-    const int c4 = (tid % (NR / 4)) * 4, rstep = kTcThreads / (NR / 4);
-    for (int f = 0; f < nf; ++f) {
-      const int s = f % TS::NST1;
-      ok = __syncthreads_and(ok && bar_wait_upto(bar1 + 8 * s, t1[s], (uint32_t)(f / TS::NST1))) != 0;
-      if (!ok) break;
-      const int nrb = (int)(fill_bytes(f) / (NR * 4));
-      const float* st = reinterpret_cast<const float*>(tsm + s * TS::STAGE);
-      for (int r = tid / (NR / 4); r < nrb; r += rstep) {
-        const float4 v = *reinterpret_cast<const float4*>(st + r * NR + c4);
-        mx[0] = max(mx[0], __float_as_uint(v.x) & 0x7FFFFFFFu);
-        mx[1] = max(mx[1], __float_as_uint(v.y) & 0x7FFFFFFFu);
-        mx[2] = max(mx[2], __float_as_uint(v.z) & 0x7FFFFFFFu);
-        mx[3] = max(mx[3], __float_as_uint(v.w) & 0x7FFFFFFFu);
+  BarTrack t1[TS::NST1], t2[kTcNraw], tm[2];
+  // ---- pass 1 (workers): column maxima over the block's rows
+  if (worker) {
+    if (ok) {
+      if (tid == 0)
+        for (int f = 0; f < min(nf, TS::NST1); ++f)
+          bulk_load(smem_u32(tsm + f * TS::STAGE), fill_src(f), fill_bytes(f), bar1 + 8 * f);
+      for (int f = 0; f < min(nf, TS::NST1); ++f) t1[f].issued = 1;
+      unsigned mx[4] = {0u, 0u, 0u, 0u};  // bits of |x|: they order as |x|, NaN above +inf
+      const int c4 = (tid % (NR / 4)) * 4, rstep = kTcWorkers / (NR / 4);
+      for (int f = 0; f < nf; ++f) {
+        const int s = f % TS::NST1;
+        ok = workers_and(ok && bar_wait_upto(bar1 + 8 * s, t1[s], (uint32_t)(f / TS::NST1)));
+        if (!ok) break;
+        const int nrb = (int)(fill_bytes(f) / (NR * 4));
+        const float* st = reinterpret_cast<const float*>(tsm + s * TS::STAGE);
+        for (int r = tid / (NR / 4); r < nrb; r += rstep) {
+          const float4 v = *reinterpret_cast<const float4*>(st + r * NR + c4);
+          mx[0] = max(mx[0], __float_as_uint(v.x) & 0x7FFFFFFFu);
+          mx[1] = max(mx[1], __float_as_uint(v.y) & 0x7FFFFFFFu);
+          mx[2] = max(mx[2], __float_as_uint(v.z) & 0x7FFFFFFFu);
+          mx[3] = max(mx[3], __float_as_uint(v.w) & 0x7FFFFFFFu);
+        }
+        workers_sync();  // stage s consumed
+        if (f + TS::NST1 < nf) {
+          if (tid == 0)
+            bulk_load(smem_u32(tsm + s * TS::STAGE), fill_src(f + TS::NST1), fill_bytes(f + TS::NST1), bar1 + 8 * s);
+          ++t1[s].issued;
+        }
       }
-      __syncthreads();  // stage s consumed
-      if (f + TS::NST1 < nf) {
-        if (tid == 0)
-          bulk_load(smem_u32(tsm + s * TS::STAGE), fill_src(f + TS::NST1), fill_bytes(f + TS::NST1), bar1 + 8 * s);
-        ++t1[s].issued;
-      }
-    }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) atomicMax(&cmax[c4 + u], mx[u]);
+      for (int u = 0; u < 4; ++u) atomicMax(&cmax[c4 + u], mx[u]);
+    }
+    if (!ok) {
+      for (int s = 0; s < TS::NST1; ++s) bar_drain(bar1 + 8 * s, t1[s]);
+      if (tid == 0) *abort_flag = 1u;
+    }
+    workers_sync();
+    if (tid < NR) {
+      const float m = __uint_as_float(cmax[tid]);
+      int E = 0;
+      if (m > 0.f && m <= 3.0e38f) frexpf(m, &E);  // m < 2^E; non-finite columns keep E = 0 and stay non-finite
+      cexp[tid] = E;
+    }
+    // the stacks read past the seventh slice: that one stays zero
+    for (int e = tid; e < 2 * TS::SLICE_BYTES / 16; e += kTcWorkers) {
+      const int bsel = e / (TS::SLICE_BYTES / 16), off = e % (TS::SLICE_BYTES / 16);
+      reinterpret_cast<uint4*>(slices + bsel * TS::SLICEBUF + kTcSlices * TS::SLICE_BYTES)[off] = make_uint4(0, 0, 0, 0);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (!ok)
-    for (int s = 0; s < TS::NST1; ++s) bar_drain(bar1 + 8 * s, t1[s]);
   __syncthreads();
-  if (tid < NR) {
-    const float m = __uint_as_float(cmax[tid]);
-    int E = 0;
-    if (m > 0.f && m <= 3.0e38f) frexpf(m, &E);  // m < 2^E; non-finite columns keep E = 0 and stay non-finite
-    cexp[tid] = E;
-  }
-  // the stacked operands read past the seventh slice: those stay zero
-  for (int e = tid; e < 2 * (TS::NSLICE - kTcSlices) * TS::SLICE_BYTES / 16; e += kTcThreads) {
-    const int bsel = e / ((TS::NSLICE - kTcSlices) * TS::SLICE_BYTES / 16);
-    const int off = e % ((TS::NSLICE - kTcSlices) * TS::SLICE_BYTES / 16);
-    reinterpret_cast<uint4*>(slices + bsel * TS::SLICEBUF + kTcSlices * TS::SLICE_BYTES)[off] = make_uint4(0, 0, 0, 0);
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  __syncthreads();
+  ok = ok && *abort_flag == 0u;
 
-  // ---- pass 2: slices, products, read-backs
-  // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, M = 128, N = NR
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-  BarTrack t2[2], tm[2];
-  unsigned live = 0;  // accumulators written since their restart (thread 0)
-  // this thread's tensor-memory lane and columns: lane quadrant warp % 4, column half warp / 4
-  const int qd = warp & 3, half = warp >> 2;
-  const int mrow = 32 * qd + lane, qr = mrow / NR;
+  // ---- pass 2
+  // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, M = N = 128
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  // worker's tensor-memory lane (quadrant warp % 4) and column half (warp / 4)
+  const int qd = warp & 3, half = (warp >> 2) & 1;
+  const int mrow = 32 * qd + lane, br = mrow / NR;
   const uint32_t tlane = tbase + ((uint32_t)(32 * qd) << 16);
-  float hi[TS::NCOL], lo[TS::NCOL];
+  float hi[NR], lo[NR];
 #pragma unroll
-  for (int i = 0; i < TS::NCOL; ++i) hi[i] = lo[i] = 0.f;
-  // read back accumulators T_ta .. T_tb into the (hi, lo) sums
-  auto readback = [&](int ta, int tb) {
+  for (int i = 0; i < NR; ++i) hi[i] = lo[i] = 0.f;
+  // read back every accumulator into the (hi, lo) sums of entries (j, k)
+  auto readback = [&]() {
 #pragma unroll
-    for (int g = 0; g < TS::NCOL / 16; ++g) {
-      const int cb = (half * (TS::NCOL / 16) + g) * 16;
-      for (int t = ta; t <= tb; ++t) {
+    for (int a = 0; a < TS::NACC; ++a) {
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
         float v[16];
-        tmem_ld16(tlane + (uint32_t)((t - 2) * NR + cb), v);
-        const float w = pow2f(-7 * (t + qr));
+        tmem_ld16(tlane + (uint32_t)(a * kTcN + 64 * half + 16 * g), v);
+        const int bc = (64 * half + 16 * g) / NR;                 // block column
+        const float w = pow2f(-7 * (2 + a * TS::G + br + bc));    // diagonal t + r + c
+        const int k0 = (16 * g) % NR;                             // 64 * half is a multiple of NR
 #pragma unroll
-        for (int i = 0; i < 16; ++i) two_sum_acc(hi[g * 16 + i], lo[g * 16 + i], __fmul_rn(v[i], w));
+        for (int i = 0; i < 16; ++i) two_sum_acc(hi[k0 + i], lo[k0 + i], __fmul_rn(v[i], w));
       }
-#pragma unroll
-      for (int i = 0; i < 16; ++i) renorm(hi[g * 16 + i], lo[g * 16 + i]);
     }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) renorm(hi[i], lo[i]);
   };
 
-  if (ok && nf > 0) {
-    if (tid == 0)
-      for (int f = 0; f < min(nf, 2); ++f) bulk_load(smem_u32(raw + f * TS::STAGE), fill_src(f), fill_bytes(f), bar2 + 8 * f);
-    for (int f = 0; f < min(nf, 2); ++f) t2[f].issued = 1;
+  if (!worker) {
+    // ---- the issuing warp: copies and products
+    if (lane == 0 && ok && nf > 0) {
+      uint32_t niss[kTcNraw + 2] = {};
+      for (int f = 0; f < min(nf, kTcNraw); ++f) {
+        bulk_load(smem_u32(raw + f * TS::STAGE), fill_src(f), fill_bytes(f), bar2 + 8 * f);
+        ++niss[f];
+      }
+      BarTrack ty[2];
+      unsigned live = 0;  // accumulators written since their restart
+      for (int f = 0; f < nf; ++f) {
+        const int b = f & 1;
+        if (!bar_wait_upto(bary + 8 * b, ty[b], (uint32_t)(f >> 1))) {  // workers sliced fill f
+          *abort_flag = 1u;
+          break;
+        }
+        if (*abort_flag) break;
+        tc_fence_after();
+        if (f + kTcNraw < nf) {  // raw stage f % kTcNraw was consumed by the slicing of fill f
+          const int st = f % kTcNraw;
+          bulk_load(smem_u32(raw + st * TS::STAGE), fill_src(f + kTcNraw), fill_bytes(f + kTcNraw), bar2 + 8 * st);
+          ++niss[st];
+        }
+        if (f % TS::PERIOD_FILLS == 0) live = 0u;
+        // descriptors differ only in the start-address field, which stays below 2^14 (16-byte
+        // units of shared memory), so each is the buffer's descriptor plus a constant
+        const uint64_t d0 = smem_desc(smem_u32(slices + b * TS::SLICEBUF), 128, TS::SBO);
+#pragma unroll
+        for (int p = 1; p <= 7; p += TS::G)
+#pragma unroll
+          for (int q = 1; p + q <= 8; q += TS::G) {
+            const int a = (p + q - 2) / TS::G;
+            const uint32_t dcol = tbase + (uint32_t)(a * kTcN);
+            const uint32_t first = (live >> a) & 1u;
+#pragma unroll
+            for (int ks = 0; ks < kTcKB / 16; ++ks) {
+              const uint64_t ad = d0 + (uint64_t)(((p - 1) * TS::SLICE_BYTES + ks * 256) >> 4);
+              const uint64_t bd = d0 + (uint64_t)(((q - 1) * TS::SLICE_BYTES + ks * 256) >> 4);
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(ks == 0 ? first : 1u)
+                  : "memory");
+            }
+            live |= 1u << a;
+          }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(barm + 8 * b)
+                     : "memory");
+        ++niss[kTcNraw + b];
+      }
+      for (int i = 0; i < kTcNraw + 2; ++i) iss[i] = niss[i];
+    }
+  } else if (ok && nf > 0) {
+    // ---- the workers: slices and read-backs
     for (int f = 0; f < nf; ++f) {
-      const int b = f & 1;
-      bool w = bar_wait_upto(bar2 + 8 * b, t2[b], (uint32_t)(f >> 1));  // raw rows of fill f
+      const int b = f & 1, st = f % kTcNraw;
+      bool w = bar_wait_upto(bar2 + 8 * st, t2[st], (uint32_t)(f / kTcNraw));  // raw rows of fill f
       if (f >= 2) w = w && bar_wait_upto(barm + 8 * b, tm[b], (uint32_t)((f - 2) >> 1));  // slices b free
-      ok = __syncthreads_and(ok && w) != 0;
-      if (!ok) break;
+      ok = workers_and(ok && w && *abort_flag == 0u);
+      if (!ok) {
+        if (tid == 0) *abort_flag = 1u;
+        mbar_arrive(bary + 8 * b);  // the issuing warp waits for this fill: let it see the abort
+        break;
+      }
       tc_fence_after();
       // slices of fill f: task (column m, 8-row group g); rows past the range are zero
       const int nrb = (int)(fill_bytes(f) / (NR * 4));
-      const float* rw = reinterpret_cast<const float*>(raw + b * TS::STAGE);
+      const float* rw = reinterpret_cast<const float*>(raw + st * TS::STAGE);
       unsigned char* sb = slices + b * TS::SLICEBUF;
-      for (int e = tid; e < NR * (kTcKB / 8); e += kTcThreads) {
+      for (int e = tid; e < NR * (kTcKB / 8); e += kTcWorkers) {
         const int m = e % NR, g = e / NR;
         const int E = cexp[m], Eh = E / 2;
         const float sc1 = pow2f(-Eh), sc2 = pow2f(Eh - E);
@@ -329,118 +418,95 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           t[i] = k < nrb ? __fmul_rn(__fmul_rn(rw[k * NR + m], sc1), sc2) : 0.f;
         }
         unsigned char* dst = sb + (m / 8) * TS::SBO + g * 128 + (m % 8) * 16;
+        // digit: rint(128 t) as (128 t + 1.5 2^23) - 1.5 2^23 (|128 t| <= 128 < 2^22, so exact
+        // round-to-nearest), remainder 128 t - s exactly; an integer of at most 8 bits has its
+        // BF16 value in the upper half of its FP32 bits
+        constexpr float kMagic = 12582912.0f;
 #pragma unroll
         for (int p = 0; p < kTcSlices; ++p) {
           uint32_t wv[4];
 #pragma unroll
           for (int i = 0; i < 8; i += 2) {
-            const float v0 = __fmul_rn(t[i], 128.f), v1 = __fmul_rn(t[i + 1], 128.f);
-            const float s0 = truncf(v0), s1 = truncf(v1);
-            t[i] = __fsub_rn(v0, s0);
-            t[i + 1] = __fsub_rn(v1, s1);
-            const __nv_bfloat162 pr = __floats2bfloat162_rn(s0, s1);
-            wv[i / 2] = *reinterpret_cast<const uint32_t*>(&pr);
+            const float s0 = __fsub_rn(__fmaf_rn(t[i], 128.f, kMagic), kMagic);
+            const float s1 = __fsub_rn(__fmaf_rn(t[i + 1], 128.f, kMagic), kMagic);
+            t[i] = __fmaf_rn(t[i], 128.f, -s0);
+            t[i + 1] = __fmaf_rn(t[i + 1], 128.f, -s1);
+            wv[i / 2] = __byte_perm(__float_as_uint(s0), __float_as_uint(s1), 0x7632);
           }
           *reinterpret_cast<uint4*>(dst + p * TS::SLICE_BYTES) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_fence_before();
-      __syncthreads();  // slices written, raw b consumed
-      tc_fence_after();
-      if (f + 2 < nf) {
-        if (tid == 0) bulk_load(smem_u32(raw + b * TS::STAGE), fill_src(f + 2), fill_bytes(f + 2), bar2 + 8 * b);
-        ++t2[b].issued;
-      }
-      if (tid == 0) {
-        const uint32_t s0 = smem_u32(sb);
-        for (int q = 1; q <= kTcSlices; ++q)
-          for (int p = 1; p + q <= 8; p += TS::G) {
-            const int t = p + q;
-            const uint32_t dcol = tbase + (uint32_t)((t - 2) * NR);
-#pragma unroll
-            for (int ks = 0; ks < kTcKB / 16; ++ks) {
-              const uint64_t ad = smem_desc(s0 + (p - 1) * TS::SLICE_BYTES + ks * 256, 128, TS::SBO);
-              const uint64_t bd = smem_desc(s0 + (q - 1) * TS::SLICE_BYTES + ks * 256, 128, TS::SBO);
-              const uint32_t accum = (live >> t) & 1u;
-              asm volatile(
-                  "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
-                  : "memory");
-              live |= 1u << t;
-            }
-          }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(barm + 8 * b)
-                     : "memory");
-      }
-      ++tm[b].issued;
-      if ((f + 1) % TS::PERIOD_FILLS == 0 && f + 1 < nf) {  // restart T_2 .. T_5
-        ok = __syncthreads_and(ok && bar_wait_upto(barm + 8 * b, tm[b], (uint32_t)(f >> 1))) != 0;
-        if (!ok) break;
+      mbar_arrive(bary + 8 * b);  // fill f sliced
+      if ((f + 1) % TS::PERIOD_FILLS == 0 && f + 1 < nf) {  // read back and restart every accumulator
+        ok = workers_and(ok && bar_wait_upto(barm + 8 * b, tm[b], (uint32_t)(f >> 1)));
+        if (!ok) {
+          if (tid == 0) *abort_flag = 1u;
+          mbar_arrive(bary + 8 * ((f + 1) & 1));  // the issuing warp waits for fill f + 1
+          break;
+        }
         tc_fence_after();
-        readback(2, 5);
+        readback();
         tc_fence_before();
-        __syncthreads();
-        if (tid == 0) live &= ~0x3Cu;
       }
     }
     if (ok) {
       const int fl = nf - 1;
-      ok = __syncthreads_and(bar_wait_upto(barm + 8 * (fl & 1), tm[fl & 1], (uint32_t)(fl >> 1))) != 0;
+      ok = workers_and(bar_wait_upto(barm + 8 * (fl & 1), tm[fl & 1], (uint32_t)(fl >> 1)));
     }
     if (ok) {
       tc_fence_after();
-      readback(2, 8);
-    }
-  }
-  if (!ok) {  // let every copy and product in flight land before the memory is released
-    for (int b = 0; b < 2; ++b) {
-      bar_drain(bar2 + 8 * b, t2[b]);
-      bar_drain(barm + 8 * b, tm[b]);
+      readback();
     }
   }
   tc_fence_before();
   __syncthreads();
+  ok = ok && *abort_flag == 0u;
+  if (worker && !ok) {  // let every copy and product in flight land before the memory is released
+    for (int s = 0; s < kTcNraw; ++s) {
+      t2[s].issued = iss[s];
+      bar_drain(bar2 + 8 * s, t2[s]);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tm[b].issued = iss[kTcNraw + b];
+      bar_drain(barm + 8 * b, tm[b]);
+    }
+  }
   double* out = dp->gpart + lb * (int64_t)NR * NR;
   if (!ok) {
     for (int e = tid; e < NR * NR; e += kTcThreads) out[e] = __longlong_as_double(0x7ff8000000000000ll);
+  } else {
+    // ---- group sums into shared memory, then one FP64 entry each
+    float2* comb = reinterpret_cast<float2*>(tsm);  // [group][column k][row j], rows padded to NR + 1
+    if (worker) {
+      const int j = mrow % NR, grp = br * 2 + half;
+#pragma unroll
+      for (int k = 0; k < NR; ++k) comb[(grp * NR + k) * TS::CSTRIDE + j] = make_float2(hi[k], lo[k]);
+    }
     __syncthreads();
-    if (warp == 0)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TS::TALLOC) : "memory");
-    return;
-  }
-  // ---- quarter sums into shared memory, then one FP64 entry each
-  float2* comb = reinterpret_cast<float2*>(tsm);  // [quarter][column k][row j], rows padded to NR + 1
-  {
-    const int j = mrow % NR;
+    for (int e = tid; e < NR * NR; e += kTcThreads) {
+      const int j = e / NR, k = e % NR;
+      const int a = min(j, k), c = max(j, k);  // the upper triangle, mirrored: the result is symmetric
+      float H = 0.f, L = 0.f;
 #pragma unroll
-    for (int i = 0; i < TS::NCOL; ++i) {
-      const int k = half * TS::NCOL + i;
-      comb[(qr * NR + k) * TS::CSTRIDE + j] = make_float2(hi[i], lo[i]);
+      for (int r = 0; r < TS::NQ; ++r) {
+        const float2 v = comb[(r * NR + c) * TS::CSTRIDE + a];
+        two_sum_acc(H, L, v.x);
+        two_sum_acc(H, L, v.y);
+      }
+      renorm(H, L);
+      const int sc = cexp[a] + cexp[c];
+      out[e] = f32_scaled_to_f64(H, sc) + f32_scaled_to_f64(L, sc);
     }
   }
+  tc_fence_before();
   __syncthreads();
-  for (int e = tid; e < NR * NR; e += kTcThreads) {
-    const int j = e / NR, k = e % NR;
-    const int a = min(j, k), c = max(j, k);  // the upper triangle, mirrored: the result is symmetric
-    float H = 0.f, L = 0.f;
-#pragma unroll
-    for (int r = 0; r < TS::G; ++r) {
-      const float2 v = comb[(r * NR + c) * TS::CSTRIDE + a];
-      two_sum_acc(H, L, v.x);
-      two_sum_acc(H, L, v.y);
-    }
-    renorm(H, L);
-    const int s = cexp[a] + cexp[c];
-    out[e] = f32_scaled_to_f64(H, s) + f32_scaled_to_f64(L, s);
-  }
-  __syncthreads();
-  if (warp == 0)
+  if (warp == kTcWorkers / 32)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TS::TALLOC) : "memory");
 }
 
-bool gram_on_tensor_cores(int Rp) { return Rp == 32 || Rp == 64; }
+bool gram_on_tensor_cores(int Rp, int64_t I) { return (Rp == 32 || Rp == 64) && I * Rp >= (int64_t)1 << 20; }
 
 int gram_tc_blocks(int64_t I) {
   const int64_t want = (I + kTcMinRows - 1) / kTcMinRows;

@@ -33,10 +33,11 @@ void launch_pass1(const StepDesc* d_descs, const int64_t* d_base, int njobs, int
                   cudaStream_t st);
 void launch_pass2(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, size_t smem,
                   cudaStream_t st);
-void launch_gram(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+void launch_gram(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp, bool tc,
                  cudaStream_t st);
-// Gram on the tensor cores (gram_tc.cu) for padded ranks 32 and 64: exact BF16 split, FP64 result
-bool gram_on_tensor_cores(int Rp);
+// Gram on the tensor cores (gram_tc.cu) for padded ranks 32 and 64 and tall factors (I Rp >= 2^20;
+// below that its fixed per-block cost loses to the FP32-pipe Gram): exact BF16 split, FP64 result
+bool gram_on_tensor_cores(int Rp, int64_t I);
 int gram_tc_blocks(int64_t I);  // blocks (per-block partials) of one Gram on the tensor cores
 void launch_gram_tc(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
                     cudaStream_t st);

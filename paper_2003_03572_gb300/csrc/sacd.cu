@@ -59,7 +59,8 @@ struct ModeData {
   float* M = nullptr;
   double* gram = nullptr;
   int64_t p1_blocks = 0, p2_blocks = 0, gram_blocks = 0, sel_chunks = 0;
-  int sel_rt = 1;  // rows per thread of the fused select/update kernel for this mode
+  int sel_rt = 1;        // rows per thread of the fused select/update kernel for this mode
+  bool gram_tc = false;  // this mode's Gram runs on the tensor cores
 };
 
 struct Prof {
@@ -291,7 +292,7 @@ void enqueue_fit_mttkrp(sacd_ctx* c) {
 
 void enqueue_gram(sacd_ctx* c, int n) {
   KScope k(c, K_GRAM);
-  launch_gram(c->ddesc + n, c->zero64, 1, c->m[n].gram_blocks, c->Rp, c->st);
+  launch_gram(c->ddesc + n, c->zero64, 1, c->m[n].gram_blocks, c->Rp, c->m[n].gram_tc, c->st);
   launch_gram_reduce(c->ddesc + n, c->zero64, 1, gram_reduce_blocks(c->Rp), c->st);
 }
 
@@ -346,7 +347,7 @@ void enqueue_iteration_dag(sacd_ctx* c) {
     enqueue_select_update(c, n, c->st);
     cudaEventRecord(ev[N + 1 + n], c->st);
     cudaStreamWaitEvent(c->side, ev[N + 1 + n], 0);
-    launch_gram(dd, c->zero64, 1, md.gram_blocks, c->Rp, c->side);
+    launch_gram(dd, c->zero64, 1, md.gram_blocks, c->Rp, md.gram_tc, c->side);
     launch_gram_reduce(dd, c->zero64, 1, gram_reduce_blocks(c->Rp), c->side);
     if (n + 1 < N) {
       launch_hl(c->ddesc + n + 1, 1, c->side);
@@ -806,7 +807,8 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     md.p2_blocks = (I + RB2 - 1) / RB2;
     md.sel_rt = selupd_choose_rt(I, Rp);
     md.sel_chunks = selupd_chunks(I, Rp, md.sel_rt);
-    md.gram_blocks = gram_on_tensor_cores(Rp) ? gram_tc_blocks(I) : std::min<int64_t>((I + CH - 1) / CH, 4 * 152);
+    md.gram_tc = gram_on_tensor_cores(Rp, I);
+    md.gram_blocks = md.gram_tc ? gram_tc_blocks(I) : std::min<int64_t>((I + CH - 1) / CH, 4 * 152);
     p1_max = std::max(p1_max, md.p1_blocks);
     gb_max = std::max(gb_max, md.gram_blocks);
     TRY(dalloc(c, &md.A, (size_t)I * Rp));
@@ -1471,6 +1473,7 @@ namespace {
 
 struct PlanClass {
   int rv = 0, nother = 0, Rp = 0, prec = 0;
+  bool gram_tc = false;
   int njobs = 0;
   StepDesc* d_descs = nullptr;
   int64_t* d_tile_base = nullptr;
@@ -1575,12 +1578,14 @@ struct BatchPlan {
       TRY(alloc_copy(&pm.d_p1, prefix(p1), st));
       TRY(alloc_copy(&pm.d_p2, prefix(p2), st));
       TRY(alloc_copy(&pm.d_gr, prefix(gr), st));
-      // width classes for the MTTKRP (rv, number of other modes, precision) and the Gram (Rp)
+      // width classes for the MTTKRP (rv, number of other modes, precision) and the Gram (Rp, and
+      // whether it runs on the tensor cores)
       std::vector<std::vector<sacd_ctx*>> groups;
       for (sacd_ctx* c : pm.jobs) {
         bool placed = false;
         for (auto& gcls : groups)
-          if (gcls[0]->rv == c->rv && gcls[0]->N == c->N && gcls[0]->prec == c->prec && gcls[0]->Rp == c->Rp) {
+          if (gcls[0]->rv == c->rv && gcls[0]->N == c->N && gcls[0]->prec == c->prec && gcls[0]->Rp == c->Rp &&
+              gcls[0]->m[n].gram_tc == c->m[n].gram_tc) {
             gcls.push_back(c);
             placed = true;
             break;
@@ -1593,6 +1598,7 @@ struct BatchPlan {
         pc.nother = gcls[0]->N - 1;
         pc.Rp = gcls[0]->Rp;
         pc.prec = gcls[0]->prec;
+        pc.gram_tc = gcls[0]->m[n].gram_tc;
         pc.njobs = (int)gcls.size();
         std::vector<StepDesc> cd;
         std::vector<int64_t> tl, gb;
@@ -1646,7 +1652,7 @@ struct BatchPlan {
         launch_pass2(pm.d_descs, pm.d_p2, pm.njobs, pm.p2, pm.smem, st);
       }
       for (const PlanClass& pc : pm.classes)
-        launch_gram(pc.d_descs, pc.d_gram_base, pc.njobs, pc.gram_blocks, pc.Rp, st);
+        launch_gram(pc.d_descs, pc.d_gram_base, pc.njobs, pc.gram_blocks, pc.Rp, pc.gram_tc, st);
       launch_gram_reduce(pm.d_descs, pm.d_gr, pm.njobs, pm.gr, st);
     }
   }

@@ -585,10 +585,10 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const StepDesc* __rest
   if (p == 0 && e < (int64_t)Rp * Rp) dp->gram_out[e] = red[0][threadIdx.x & 31];
 }
 
-void launch_gram(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
+void launch_gram(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp, bool tc,
                  cudaStream_t st) {
   if (total_blocks <= 0) return;
-  if (gram_on_tensor_cores(Rp)) {
+  if (tc) {
     launch_gram_tc(d_descs, d_base, njobs, total_blocks, Rp, st);
     return;
   }

@@ -75,3 +75,27 @@ def test_batch_of_small_ranks_only():
                 for n in range(3):
                     np.testing.assert_array_equal(b.factor(j, n), a.factor(n))
                 assert (obj[j], fit[j]) == a.fit()
+
+
+def test_batch_mixes_tensor_core_and_fp32_grams():
+    """Jobs of one padded rank whose mode-0 factors are tall (Gram on the tensor cores, I Rp >=
+    2^20) or short (FP32-pipe Gram) run in one batch: the launch splits them by Gram kind, every
+    result stays bit-identical to the job alone, and each Gram of the final factors matches the
+    FP64 oracle within 1e-10."""
+    specs = []
+    shapes = [((40000, 300, 50), 32), ((3000, 200, 40), 32), ((20000, 500, 30), 64), ((5000, 400, 20), 64)]
+    for j, (dims, R) in enumerate(shapes):
+        idx, vals = synth.sparse_tensor(dims, 20000 + 5000 * j, dist="zipf", zipf_s=1.1, seed=60 + j)
+        specs.append(dict(dims=dims, idx=idx, vals=vals, rank=R, init=synth.init_factors(dims, R, 60 + j)))
+    with S.SaCDBatch(specs) as b:
+        b.iterate(3)
+        obj, fit = b.fit()
+        for j, sp in enumerate(specs):
+            with S.SaCD(sp["dims"], sp["idx"], sp["vals"], sp["rank"], sp["init"]) as a:
+                a.iterate(3)
+                for n in range(3):
+                    F = a.factor(n)
+                    np.testing.assert_array_equal(b.factor(j, n), F)
+                    ref = O.gram(F)
+                    assert np.linalg.norm(a.tap("GRAM", n) - ref) <= 1e-10 * np.linalg.norm(ref)
+                assert (obj[j], fit[j]) == a.fit()
