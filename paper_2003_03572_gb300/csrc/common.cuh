@@ -83,9 +83,10 @@ struct StepDesc {
 };
 
 // Grid barrier words of one persistent launch (count, generation, error word: nonzero after a
-// bounded wait gave up).
+// bounded wait gave up) and its two work queues (next item of phase 1 and of phase 2; the launch
+// empties each when no block can still take from it).
 struct GridBar {
-  unsigned int count, gen, err, pad;
+  unsigned int count, gen, err, queue1, queue2, pad[3];
 };
 
 // Result of the objective evaluation (sacd_fit).

@@ -1623,7 +1623,7 @@ struct BatchPlan {
     for (auto x : fb) fit_blocks += x;
     std::vector<double> zeros((size_t)njobs * 4, 0.0);
     TRY(alloc_copy(&d_fit_out, zeros, st));
-    TRY(alloc_copy(&d_bar, std::vector<GridBar>(1, GridBar{0u, 0u, 0u, 0u}), st));
+    TRY(alloc_copy(&d_bar, std::vector<GridBar>(1, GridBar{}), st));
     for (int j = 0; j < njobs; ++j) {
       fds[j].out = d_fit_out + 4 * j;
       fds[j].wait_err = &d_bar->err;
