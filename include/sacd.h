@@ -313,21 +313,26 @@ void sacd_batch_destroy(sacd_batch* b);
 
 /*
  * Serving (not in the paper; the served workload): continuous batching of factorisation jobs
- * on one GPU, single-threaded API.
+ * on one GPU, single-threaded API (one host thread calls it; internally a preparation thread
+ * creates the contexts of admitted jobs on a stream of its own, so that the H2D copies and
+ * sorts of new jobs overlap the iterations of running ones).
  *  - sacd_server_create: `hbm_budget_bytes` caps the device memory of admitted jobs (each job is
  *    charged an upper bound of its create-time peak until it is admitted, then the bytes its
  *    context holds); at most `max_active` jobs run at once and at most `max_admit_per_step` are
- *    admitted per step; `stream` as for contexts.
+ *    admitted per step; `stream` as for contexts (the iterations run on it).
  *  - sacd_server_submit: queue a job (FIFO) that will run `iters` outer iterations. The arrays
- *    that cfg points to are read when the job is admitted and must stay valid until its result
- *    has been drained by sacd_server_results. cfg->stream is ignored.
- *  - sacd_server_step: admit waiting jobs in order while they fit the budget (a job larger than
- *    the whole budget finishes with SACD_ENOMEM; a job whose create fails finishes with that
- *    status), run one outer iteration of every admitted job with one batched launch set, and
+ *    that cfg points to are read when the job's context is created, after its admission, and
+ *    must stay valid until its result has been drained by sacd_server_results. cfg->stream is
+ *    ignored.
+ *  - sacd_server_step: add the jobs whose contexts are ready to the running set; admit waiting
+ *    jobs in order while they fit the budget, handing them to the preparation thread (a job
+ *    larger than the whole budget finishes with SACD_ENOMEM; a job whose create fails finishes
+ *    with that status at a later step); if nothing is running yet, wait for the first context;
+ *    run one outer iteration of every running job with one batched launch set, and
  *    finish the jobs that reached their iteration count: objective and fit evaluated, factors
  *    copied to host memory, device memory freed (a job whose objective is not finite finishes
- *    with SACD_ESTATE and no factors). Waits for the GPU. Reports active and waiting counts
- *    (nullable).
+ *    with SACD_ESTATE and no factors). Waits for the iteration stream. Reports active (running or
+ *    being created) and waiting counts (nullable).
  *  - sacd_server_results: drain up to `cap` finished jobs' results (times are seconds since the
  *    server was created, host clock); their factors stay available through
  *    sacd_server_get_factor (I_n x R FP32) until sacd_server_release.
@@ -345,8 +350,9 @@ typedef struct {
   char error[128];
 } sacd_job_result;
 typedef struct {
-  int32_t active, waiting, finished;
+  int32_t active, waiting, finished;   /* active counts running jobs and jobs being created */
   int64_t used_bytes, peak_bytes, budget_bytes, steps;
+  int32_t creating;                    /* admitted jobs whose contexts are not ready yet */
 } sacd_server_stats_t;
 sacd_status sacd_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t max_admit_per_step,
                                void* stream, sacd_server** out);

@@ -516,12 +516,12 @@ int gram_tc_blocks(int64_t I) {
 void launch_gram_tc(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_blocks, int Rp,
                     cudaStream_t st) {
   if (total_blocks <= 0) return;
-  static bool configured = false;
-  if (!configured) {
+  static const bool configured = [] {  // once per process, thread-safe
     cudaFuncSetAttribute(gram_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcShape<32>::SMEM);
     cudaFuncSetAttribute(gram_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcShape<64>::SMEM);
-    configured = true;
-  }
+    return true;
+  }();
+  (void)configured;
   if (Rp == 32)
     gram_tc_kernel<32><<<(unsigned)total_blocks, kTcThreads, TcShape<32>::SMEM, st>>>(d_descs, d_base, njobs);
   else

@@ -9,8 +9,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <condition_variable>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "sacd.h"
@@ -666,6 +669,8 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     // keep freed blocks of the stream-ordered pool cached in this process (a process-local pool
     // attribute, not a device setting): contexts created and destroyed back to back reuse them
     static bool pool_done[64] = {};
+    static std::mutex pool_mu;  // contexts may be created from several host threads
+    std::lock_guard<std::mutex> lk(pool_mu);
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !pool_done[dev]) {
       cudaMemPool_t pool;
@@ -1820,6 +1825,7 @@ struct ServerJob {
   double t_submit = 0, t_admit = -1, t_done = -1;
   sacd_ctx* ctx = nullptr;
   int32_t status = 0;
+  sacd_status create_status = SACD_OK;  // set by the preparation thread
   std::string error;
   double objective = 0, fit = 0;
   std::vector<std::vector<float>> factors;
@@ -1864,6 +1870,18 @@ struct sacd_server {
   std::chrono::steady_clock::time_point t0;
   std::deque<ServerJob*> waiting;
   std::vector<ServerJob*> active;
+  // admitted jobs whose contexts a preparation thread creates on its own stream (H2D copies,
+  // sorts) while the iteration stream runs; they join the plan at the next step
+  int dev = 0;
+  cudaStream_t prep_st = nullptr;
+  std::thread prep;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<ServerJob*> to_create;  // guarded by mu
+  std::deque<ServerJob*> created;    // guarded by mu
+  bool stop = false;                 // guarded by mu
+  int32_t inflight = 0;              // admitted, not yet iterating (main thread)
+  int64_t reserved = 0;              // their create-time bound (main thread)
   std::deque<ServerJob*> finished;    // results not drained yet
   std::map<int64_t, ServerJob*> kept; // drained, factors kept until released
   BatchPlan plan;
@@ -1872,6 +1890,27 @@ struct sacd_server {
 };
 
 namespace {
+
+// The preparation thread: creates the contexts of admitted jobs, in admission order.
+void prep_loop(sacd_server* s) {
+  cudaSetDevice(s->dev);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    s->cv.wait(lk, [s] { return s->stop || !s->to_create.empty(); });
+    if (s->stop) return;
+    ServerJob* j = s->to_create.front();
+    s->to_create.pop_front();
+    lk.unlock();
+    j->cfg.stream = s->prep_st;
+    sacd_ctx* c = nullptr;
+    j->create_status = sacd_create(&j->cfg, &c);  // synchronises prep_st before returning
+    if (j->create_status != SACD_OK) j->error = g_err;
+    j->ctx = c;
+    lk.lock();
+    s->created.push_back(j);
+    s->cv.notify_all();
+  }
+}
 
 void finish_job(sacd_server* s, ServerJob* j) {
   j->t_done = now_s(s->t0);
@@ -1907,6 +1946,19 @@ sacd_status sacd_server_create(int64_t hbm_budget_bytes, int32_t max_active, int
       return fail(SACD_ECUDA, "cudaStreamCreate failed");
     }
     s->own_stream = true;
+  }
+  if (cudaGetDevice(&s->dev) != cudaSuccess || cudaStreamCreateWithFlags(&s->prep_st, cudaStreamNonBlocking) != cudaSuccess) {
+    if (s->own_stream) cudaStreamDestroy(s->st);
+    delete s;
+    return fail(SACD_ECUDA, "cudaStreamCreate failed");
+  }
+  try {
+    s->prep = std::thread(prep_loop, s);
+  } catch (...) {
+    cudaStreamDestroy(s->prep_st);
+    if (s->own_stream) cudaStreamDestroy(s->st);
+    delete s;
+    return fail(SACD_ENOMEM, "could not start the preparation thread");
   }
   *out = s;
   return SACD_OK;
@@ -1946,12 +1998,43 @@ sacd_status sacd_server_submit(sacd_server* s, const sacd_config* cfg, int32_t i
 sacd_status sacd_server_step(sacd_server* s, int32_t* n_active, int32_t* n_waiting) {
   if (!s) return fail(SACD_EINVAL, "null server");
   if (s->poisoned) return fail(SACD_ESTATE, "server is poisoned by an earlier CUDA error");
+  // ---- jobs whose contexts are ready join the plan; with nothing to iterate yet, wait for one
+  auto activate = [&](bool wait) -> sacd_status {
+    std::deque<ServerJob*> ready;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (wait) s->cv.wait(lk, [s] { return !s->created.empty(); });
+      ready.swap(s->created);
+    }
+    for (ServerJob* j : ready) {
+      --s->inflight;
+      s->reserved -= j->est_bytes;
+      if (j->create_status != SACD_OK) {
+        j->status = j->create_status;
+        finish_job(s, j);
+        if (j->status == SACD_ECUDA) {
+          s->poisoned = true;
+          return fail(SACD_ECUDA, "job " + std::to_string(j->id) + ": " + j->error);
+        }
+        continue;
+      }
+      j->ctx->st = s->st;  // from now on the job's work (and its frees) follow the iterations
+      j->bytes = j->ctx->device_bytes;
+      s->used += j->bytes;
+      s->active.push_back(j);
+      s->plan_dirty = true;
+    }
+    return SACD_OK;
+  };
+  TRY(activate(false));
   // ---- admission, FIFO, within the budget, at most max_admit per step (creating a context takes
-  // GPU time too; capping it keeps the admitted jobs iterating while a burst arrives)
+  // GPU time too; capping it keeps the admitted jobs iterating while a burst arrives): the
+  // preparation thread creates the contexts while the iterations below run
   int admitted = 0;
-  while (!s->waiting.empty() && (int)s->active.size() < s->max_active && admitted < s->max_admit) {
+  while (!s->waiting.empty() && (int)s->active.size() + s->inflight < s->max_active && admitted < s->max_admit) {
     ServerJob* j = s->waiting.front();
-    if (!s->active.empty() && s->used + j->est_bytes > s->budget) break;
+    const bool idle = s->active.empty() && s->inflight == 0;
+    if (!idle && s->used + s->reserved + j->est_bytes > s->budget) break;
     if (j->est_bytes > s->budget) {  // can never fit
       s->waiting.pop_front();
       j->status = SACD_ENOMEM;
@@ -1961,26 +2044,17 @@ sacd_status sacd_server_step(sacd_server* s, int32_t* n_active, int32_t* n_waiti
     }
     s->waiting.pop_front();
     j->t_admit = now_s(s->t0);
-    sacd_ctx* c = nullptr;
-    const sacd_status st = sacd_create(&j->cfg, &c);
-    if (st != SACD_OK) {
-      j->status = st;
-      j->error = g_err;
-      finish_job(s, j);
-      if (st == SACD_ECUDA) {
-        s->poisoned = true;
-        return fail(SACD_ECUDA, "job " + std::to_string(j->id) + ": " + j->error);
-      }
-      continue;
-    }
     ++admitted;
-    j->ctx = c;
-    j->bytes = c->device_bytes;
-    s->used += j->bytes;
-    s->peak_used = std::max(s->peak_used, s->used + j->est_bytes - j->bytes);
-    s->active.push_back(j);
-    s->plan_dirty = true;
+    ++s->inflight;
+    s->reserved += j->est_bytes;
+    s->peak_used = std::max(s->peak_used, s->used + s->reserved);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->to_create.push_back(j);
+    }
+    s->cv.notify_all();
   }
+  if (s->active.empty() && s->inflight > 0) TRY(activate(true));
   // ---- one outer iteration of every admitted job
   if (!s->active.empty()) {
     if (s->plan_dirty) {
@@ -2051,7 +2125,7 @@ sacd_status sacd_server_step(sacd_server* s, int32_t* n_active, int32_t* n_waiti
       return fail(SACD_ECUDA, std::string("server step: ") + cudaGetErrorString(e));
     }
   }
-  if (n_active) *n_active = (int32_t)s->active.size();
+  if (n_active) *n_active = (int32_t)s->active.size() + s->inflight;
   if (n_waiting) *n_waiting = (int32_t)s->waiting.size();
   return SACD_OK;
 }
@@ -2102,18 +2176,33 @@ sacd_status sacd_server_release(sacd_server* s, int64_t job_id) {
 
 sacd_status sacd_server_stats(sacd_server* s, sacd_server_stats_t* out) {
   if (!s || !out) return fail(SACD_EINVAL, "null argument");
-  out->active = (int32_t)s->active.size();
+  out->active = (int32_t)s->active.size() + s->inflight;
   out->waiting = (int32_t)s->waiting.size();
   out->finished = (int32_t)s->finished.size();
   out->used_bytes = s->used;
   out->peak_bytes = s->peak_used;
   out->budget_bytes = s->budget;
   out->steps = s->steps;
+  out->creating = s->inflight;
   return SACD_OK;
 }
 
 void sacd_server_destroy(sacd_server* s) {
   if (!s) return;
+  if (s->prep.joinable()) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stop = true;
+    }
+    s->cv.notify_all();
+    s->prep.join();  // returns after the context it may be creating is done
+  }
+  for (ServerJob* j : s->to_create) delete j;
+  for (ServerJob* j : s->created) {
+    if (j->ctx) sacd_destroy(j->ctx);
+    delete j;
+  }
+  if (s->prep_st) cudaStreamDestroy(s->prep_st);
   if (s->st) cudaStreamSynchronize(s->st);
   s->plan.release();
   for (ServerJob* j : s->active) {

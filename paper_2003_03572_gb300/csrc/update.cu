@@ -825,11 +825,13 @@ void launch_check_factor(const float* A, int64_t rows, int R, int Rp, unsigned i
 }
 
 void configure_kernels() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(pass1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-  cudaFuncSetAttribute(pass2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-  done = true;
+  // once per process, also when contexts are created from several host threads
+  static const bool done = [] {
+    cudaFuncSetAttribute(pass1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(pass2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    return true;
+  }();
+  (void)done;
 }
 
 }  // namespace sacd

@@ -137,6 +137,7 @@ class sacd_server_stats_t(C.Structure):
         ("peak_bytes", C.c_int64),
         ("budget_bytes", C.c_int64),
         ("steps", C.c_int64),
+        ("creating", C.c_int32),
     ]
 
 

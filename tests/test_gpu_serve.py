@@ -98,7 +98,7 @@ def test_budget_admission_and_host_failures():
     bad["idx"] = sp[0]["idx"].copy()
     bad["idx"][0, 0] = 10_000  # out of range: fails at admission, on the host side of the create
     huge = dict(dims=(100, 100, 100), idx=np.zeros((3, 1), np.int32), vals=np.ones(1, np.float32), rank=8)
-    budget = 40 << 20  # a few small jobs at a time
+    budget = 8 << 20  # two or three of these jobs at a time (each is charged 2 to 4 MB at admission)
     with serve.Server(budget) as srv:
         jobs = [srv.submit(s, 4) for s in sp[:4]] + [srv.submit(bad, 4)] + [srv.submit(s, 4) for s in sp[4:]]
         huge_spec = dict(dims=(2_000_000, 2_000_000, 2_000_000), idx=np.zeros((3, 1), np.int32),
@@ -118,7 +118,42 @@ def test_budget_admission_and_host_failures():
         assert status[jh][0] == 2
         assert all(status[j][0] == 0 for k, j in enumerate(jobs) if k != 4)
         assert srv.stats()["peak_bytes"] <= budget
-        assert max_active < len(jobs)
+        assert max_active <= 4  # running plus being created: the budget held the rest back
+
+
+def test_admission_overlaps_running_jobs():
+    """A job admitted while another runs is created by the preparation thread on its own stream:
+    steps keep iterating the running job while the new context is built (stats count it as
+    creating), the new job then joins, and both results equal their contexts run alone."""
+    small = specs(17)[0]
+    dims = (200_000, 100_000, 2_000)
+    idx, vals = synth.sparse_tensor(dims, 4_000_000, dist="zipf", zipf_s=1.1, seed=31)
+    big = dict(dims=dims, idx=idx, vals=vals, rank=16, init=synth.init_factors(dims, 16, 31))
+    with serve.Server(1 << 36) as srv:
+        ja = srv.submit(small, 400)
+        while srv.stats()["creating"] or srv.stats()["active"] == 0:
+            srv.step()
+        jb = srv.submit(big, 3)
+        steps_while_creating = 0
+        res = {}
+        while len(res) < 2:
+            srv.step()
+            st = srv.stats()
+            if st["creating"]:
+                steps_while_creating += 1
+            for r in srv.results():
+                res[r["job_id"]] = r
+                if r["status"] == 0:
+                    r["factors"] = srv.factors(r["job_id"])
+                srv.release(r["job_id"])
+    assert steps_while_creating >= 2
+    assert res[ja]["status"] == 0 and res[jb]["status"] == 0
+    for jid, sp, it in ((ja, small, 400), (jb, big, 3)):
+        with S.SaCD(sp["dims"], sp["idx"], sp["vals"], sp["rank"], sp["init"],
+                    precision=sp.get("precision", S.SACD_FP32)) as g:
+            g.iterate(it)
+            for n in range(len(sp["dims"])):
+                np.testing.assert_array_equal(res[jid]["factors"][n], g.factor(n))
 
 
 def test_poisson_arrival_driver():
