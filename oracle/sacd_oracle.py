@@ -36,6 +36,12 @@ design notes of the repository):
 * Duplicate coordinates are summed (in FP32, in their input order) before anything else.
 * The BF16-gather variant (not in the paper) is defined here as: each gathered factor value is
   the FP32 factor rounded to the nearest BF16 (ties to even); everything else is unchanged.
+* FSaCD (Algorithm 2, ``FSaCDOracle``): the column gradient of Eq. colgrad carries Eq. 9's sign,
+  g_r = (U H)_r - m_r; the column update of Eq. upur is Eq. 12's projected step,
+  u_qr <- max(0, u_qr - g_qr/h_rr), taken on the selected elements only; "z_r > 0" of the first
+  visit is elementwise; the choice between Eq. 24 and Eq. 27 compares ti = sum of z over all
+  columns, so every column's z is formed before any element moves; the parallel columns all use
+  the factor at the start of the mode step.
 
 Pins (tests/test_oracle_pins.py) tie each function here to something other than itself:
 explicit unfoldings and Khatri-Rao products, finite differences, the exact 1-D decrease, a HALS
@@ -71,6 +77,8 @@ __all__ = [
     "rmse",
     "pattern_distinctiveness",
     "SaCDOracle",
+    "sttvp",
+    "FSaCDOracle",
 ]
 
 
@@ -428,3 +436,73 @@ class SaCDOracle:
     def fit(self):
         f = self.objective()
         return f, fit_from_objective(f, self.nx_sq)
+
+
+# ----------------------------------------------------------------------------------------
+# FSaCD (Section 4.4, Algorithm 2)
+# ----------------------------------------------------------------------------------------
+
+
+def sttvp(dims, idx, vals, factors, n, r):
+    """Column r of the mode-n MTTKRP as a sparse tensor times vectors product (the column-wise
+    m_r of FSaCD): m_r[q] = sum over the nonzeros with i_n = q of x times the product of the other
+    factors' r-th entries at the nonzero's coordinates."""
+    w = np.asarray(vals, dtype=np.float64).copy()
+    for k in range(len(dims)):
+        if k != n:
+            w = w * np.asarray(factors[k], dtype=np.float64)[np.asarray(idx[k]), r]
+    m = np.zeros(int(dims[n]))
+    np.add.at(m, np.asarray(idx[n]), w)
+    return m
+
+
+class FSaCDOracle:
+    """FSaCD (Algorithm 2), generalised to N modes, with the readings listed in the module header.
+
+    Per mode step: H and L (Eq. 10, L = ||H||_F); for every column r, from the factor at the start
+    of the step, m_r by sttvp, the column gradient, the column's projected deltas and importance
+    (Eq. colgrad, Eq. 11-12, Eq. coleq); then ti (Eq. 25), the saturation test of every element
+    (first visit: z > 0; else Eq. 24 or Eq. 27) and the update of the selected ones (Eq. 13).
+    """
+
+    def __init__(self, dims, idx, vals, init):
+        self.dims = [int(d) for d in dims]
+        self.N = len(self.dims)
+        self.idx, self.vals = coalesce(self.dims, idx, vals)
+        self.A = [np.asarray(a, dtype=np.float64).copy() for a in init]
+        self.R = self.A[0].shape[1]
+        self.Zprev = [np.zeros((d, self.R)) for d in self.dims]
+        self.tiprev = [0.0] * self.N
+        self.first = [True] * self.N
+
+    def mode_step(self, n, mask=None):
+        U = self.A[n]
+        H = hadamard_of_grams(self.A, n)
+        L = float(np.linalg.norm(H))
+        h = curvatures(H)
+        Z = np.zeros_like(U)
+        S = np.zeros_like(U)
+        for r in range(self.R):  # Algorithm 2's parallel loop over columns
+            m_r = sttvp(self.dims, self.idx, self.vals, self.A, n, r)
+            g_r = U @ H[:, r] - m_r
+            if h[r] > 0:
+                S[:, r] = np.maximum(0.0, U[:, r] - g_r / h[r]) - U[:, r]
+            Z[:, r] = -g_r * S[:, r] - 0.5 * L * S[:, r] ** 2
+        ti = float(Z.sum())
+        if mask is not None:
+            sel = np.asarray(mask, dtype=bool)
+        elif self.first[n]:
+            sel = Z > 0
+        else:
+            sp = self.Zprev[n] - Z if ti > self.tiprev[n] else Z - self.Zprev[n]
+            sel = sp > 0
+        self.A[n] = np.where(sel, U + S, U)
+        self.Zprev[n] = Z
+        self.tiprev[n] = ti
+        self.first[n] = False
+        return int(np.count_nonzero(sel))
+
+    def iterate(self, iters=1):
+        for _ in range(iters):
+            for n in range(self.N):
+                self.mode_step(n)

@@ -218,6 +218,38 @@ def test_variants_replay(lnorm, fixup):
                 assert relerr(g.factor(n), o.A[n]) <= 1e-5
 
 
+def test_fsacd_on_gpu_lemma2_path():
+    """FSaCD (Algorithm 2) runs on the GPU as the Lemma 2 update: every mode step of the GPU's
+    Lemma 2 path matches the FSaCD oracle (its column-wise sttvp, gradient, importance and
+    update), from the GPU's factors and state, with the GPU's selection replayed: z within the
+    FP32 bound, the factor within 1e-5."""
+    dims, nnz, dist, s, R = CASES[2]
+    idx, vals, init = make_case(dims, nnz, dist, s, R)
+    with S.SaCD(dims, idx, vals, R, init, fixup=S.SACD_FIXUP_LEMMA2) as g:
+        g.set_debug(True)
+        o = O.FSaCDOracle(dims, idx, vals, init)
+        ref = O.SaCDOracle(dims, idx, vals, init, fixup="lemma2")  # for the FP32 bound of z only
+        for it in range(3):
+            for n in range(len(dims)):
+                F = g.factors()
+                zprev = g.tap("ZPREV", n)
+                st = g.tap("STATE", n)
+                g.mode_step(n)
+                for oo in (o, ref):
+                    oo.A = [f.astype(np.float64) for f in F]
+                    oo.Zprev[n] = zprev.astype(np.float64)
+                    oo.tiprev[n] = st[0]
+                    oo.first[n] = st[1] != 0
+                mask = g.tap("MASK", n, last_mode=n).astype(bool)
+                assert o.mode_step(n, mask=mask) == int(mask.sum())
+                ref.mode_step(n, mask=mask)
+                Zo = o.Zprev[n]
+                zs = max(np.abs(Zo).max(), 1e-30)
+                assert (np.abs(g.tap("ZPREV", n) - Zo) <= 1e-5 * zs + z_fp32_bound(F[n], ref.last)).all()
+                assert relerr(g.factor(n), o.A[n]) <= 1e-5
+                assert_rowwise(g.factor(n), o.A[n], 1e-5, np.linalg.norm(F[n].astype(np.float64), axis=1))
+
+
 def test_hand_worked_case_on_gpu():
     gd = json.load(open(os.path.join(GOLDEN, "selection_2x1x1_r2.json")))
     init = [np.array(a, dtype=np.float32) for a in gd["init"]]

@@ -427,3 +427,35 @@ def test_negligible_curvature_takes_no_step():
     # the two thresholds, at and just above them
     assert list(O.curvatures(np.diag([1.0, 2.0**-40, 2.0**-40 * 1.0001]))) == [1.0, 0.0, 2.0**-40 * 1.0001]
     assert list(O.curvatures(np.diag([1e-39, 2.0**-126, 2.0**-125]))) == [0.0, 0.0, 2.0**-125]
+
+
+@pytest.mark.parametrize("dims,R,nnz,seed", [((30, 20, 10), 5, 400, 2), ((12, 9, 7, 5), 4, 300, 3)])
+def test_sttvp_columns_equal_the_mttkrp(dims, R, nnz, seed):
+    """FSaCD's column-wise MTTKRP (sttvp) against the MTTKRP, itself pinned against the explicit
+    unfolding times the Khatri-Rao product."""
+    idx, vals, F = random_case(dims, R, nnz, seed)
+    cidx, cvals = O.coalesce(dims, idx, vals)
+    for n in range(len(dims)):
+        M = O.mttkrp(list(dims), cidx, cvals, F, n)
+        for r in range(R):
+            np.testing.assert_allclose(O.sttvp(dims, cidx, cvals, F, n, r), M[:, r], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("dims,R,nnz,seed", [((30, 20, 10), 5, 400, 4), ((12, 9, 7, 5), 4, 300, 5)])
+def test_fsacd_equals_sacd_with_lemma2_updates(dims, R, nnz, seed):
+    """Algorithm 2 (columns in parallel from the start-of-step factor) takes the same steps as
+    Algorithm 1 with the Lemma 2 reading (each selected element moves from the start-of-step
+    gradient), over several iterations and every branch of the selection."""
+    idx, vals, init = random_case(dims, R, nnz, seed)
+    a = O.SaCDOracle(dims, idx, vals, init, fixup="lemma2")
+    b = O.FSaCDOracle(dims, idx, vals, init)
+    branches = set()
+    for it in range(6):
+        for n in range(len(dims)):
+            na = a.mode_step(n)
+            nb = b.mode_step(n)
+            branches.add(a.last["branch"])
+            assert na == nb
+            np.testing.assert_allclose(b.A[n], a.A[n], rtol=1e-12, atol=1e-14)
+            np.testing.assert_allclose(b.Zprev[n], a.Zprev[n], rtol=1e-10, atol=1e-14)
+    assert branches == {"first", "eq24", "eq27"}
