@@ -17,6 +17,12 @@ void set_last_error(const char* msg);
 void launch_mttkrp(const StepDesc* d_descs, const int64_t* d_tile_base, int njobs, int64_t total_tiles, int prec,
                    int rv, int nother, cudaStream_t st);
 void launch_rowfix(const int4* light, int64_t nl, const int4* heavy, int64_t nh, int32_t* rowfix, cudaStream_t st);
+// One pass for the objective's FP32-gather MTTKRP (dF: FP32 factors, output, partials) and the
+// mode's BF16-gather MTTKRP (dB), bit-identical to launch_mttkrp with dB; BF16 rows of 4 or 8
+// vectors (padded rank 32, 64), 2 or 3 other modes (mttkrp_dual_supported).
+bool mttkrp_dual_supported(int rv, int nother);
+void launch_mttkrp_dual(const StepDesc* dB, const StepDesc* dF, int64_t total_tiles, int rv, int nother,
+                        cudaStream_t st);
 void launch_fixup_light(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st);
 void launch_fixup_chunks(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total, cudaStream_t st);
 constexpr int kFixChunk = 128;  // partials per level-1 chunk of a heavy split row

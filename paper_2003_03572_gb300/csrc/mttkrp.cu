@@ -164,8 +164,15 @@ __device__ void zero_rows(float* __restrict__ Mout, int Rp, int64_t r0, int64_t 
 
 // One warp tile. NO = number of other modes (N-1) when known at compile time, 0 = any.
 // Element positions fit in 32 bits (nnz <= 2^31 - 1); addresses are formed in 64 bits.
-template <int PREC, int RV, int NO>
-__device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpPieces& wp, int32_t* sbuf) {
+// DUAL (BF16 layout only): the rows are gathered from the FP32 master factors of `dpf`; each value
+// rounded to BF16 (round to nearest even, the BF16 mirror's own rounding) feeds the same product
+// chain as a BF16 gather, so dp's M and partials are bit for bit those of the BF16 kernel, and the
+// unrounded values feed a second chain whose sums go to dpf's M and partials (the same segments,
+// merges and tile slots).
+template <int PREC, int RV, int NO, bool DUAL = false>
+__device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpPieces& wp, int32_t* sbuf,
+                            const StepDesc* __restrict__ dpf = nullptr, WarpPieces* wpf = nullptr) {
+  static_assert(!DUAL || PREC == 1, "the dual tile keeps the BF16 layout");
   using S = TileShape<PREC, RV>;
   constexpr int MAXO = NO > 0 ? NO : SACD_MAXN - 1;
   constexpr int kUnroll = S::U;
@@ -189,6 +196,16 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
     ci[m] = dp->cidx + (int64_t)m * cstride;
     fac[m] = dp->fac[m];
   }
+  constexpr int NVF = DUAL ? TileShape<PREC, RV>::NV : 1;  // floats per lane of the second chain
+  const float* fac32[DUAL ? MAXO : 1];
+  float* __restrict__ Mf = nullptr;
+  float* __restrict__ carryf = nullptr;
+  if constexpr (DUAL) {
+#pragma unroll
+    for (int m = 0; m < MAXO; ++m) fac32[m] = static_cast<const float*>(dpf->fac[m]);
+    Mf = dpf->M;
+    carryf = dpf->carry;
+  }
   // 128-bit index loads of 4 consecutive nonzeros when every index row is 16-byte aligned
   // (tiles and sub-ranges start at multiples of 4 nonzeros)
   const bool vec = (((reinterpret_cast<uintptr_t>(rowid) | reinterpret_cast<uintptr_t>(val) |
@@ -199,8 +216,11 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
   const int b = min(a + sub, t1);
 
   float acc[S::NV];
+  float accf[NVF];
 #pragma unroll
   for (int i = 0; i < S::NV; ++i) acc[i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < NVF; ++i) accf[i] = 0.f;
   int32_t cur = -1;
   int seg = a;
   int flags = 0;
@@ -218,6 +238,7 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
         int c0;
         lane_cols<PREC, RV>(lig, k, c0);
         store_row_chunk<S::W>(Mrow, c0, acc + k * S::W);
+        if constexpr (DUAL) store_row_chunk<S::W>(Mf + (int64_t)row * Rp, c0, accf + k * S::W);
       }
     } else {
       const int slot = lopen ? 0 : 1;
@@ -228,6 +249,11 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
         lane_cols<PREC, RV>(lig, k, c0);
 #pragma unroll
         for (int i = 0; i < S::W; ++i) dst[c0 + i] = acc[k * S::W + i];
+        if constexpr (DUAL) {
+          float* dstf = &wpf->acc[slot][0] + (g * Rp);
+#pragma unroll
+          for (int i = 0; i < S::W; ++i) dstf[c0 + i] = accf[k * S::W + i];
+        }
       }
       if (lig == 0) wp.row[slot][g] = row;
       flags |= lopen ? (ropen ? 3 : 1) : 4;
@@ -237,18 +263,36 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
   // gathers, products and row accumulation of the nonzeros e0 .. e0+kUnroll-1 below `lim`
   auto consume = [&](int e0, const int32_t* rows, const float* xs, const uint32_t (*ix)[kUnroll], int lim) {
     float prod[kUnroll][S::NV];
+    float prodf[kUnroll][NVF];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       if (e0 + u < lim) {
 #pragma unroll
         for (int i = 0; i < S::NV; ++i) prod[u][i] = xs[u];
+        if constexpr (DUAL) {
+#pragma unroll
+          for (int i = 0; i < NVF; ++i) prodf[u][i] = xs[u];
+        }
 #pragma unroll
         for (int m = 0; m < MAXO; ++m) {
           if (NO > 0 || m < nother) {
 #pragma unroll
             for (int k = 0; k < S::CPL; ++k) {
               float v[S::W];
-              GatherVec<PREC>::load(fac[m], (int64_t)ix[m][u] * RV + lig + k * S::LPR, v);
+              if constexpr (DUAL) {
+                int c0;
+                lane_cols<PREC, RV>(lig, k, c0);
+                const float4* src = reinterpret_cast<const float4*>(fac32[m] + (int64_t)ix[m][u] * Rp + c0);
+                const float4 f0 = __ldg(src), f1 = __ldg(src + 1);
+                const float vf[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+                for (int i = 0; i < S::W; ++i) v[i] = __bfloat162float(__float2bfloat16_rn(vf[i]));
+#pragma unroll
+                for (int i = 0; i < S::W; i += 2)
+                  mul2_inplace(prodf[u][k * S::W + i], prodf[u][k * S::W + i + 1], vf[i], vf[i + 1]);
+              } else {
+                GatherVec<PREC>::load(fac[m], (int64_t)ix[m][u] * RV + lig + k * S::LPR, v);
+              }
 #pragma unroll
               for (int i = 0; i < S::W; i += 2)
                 mul2_inplace(prod[u][k * S::W + i], prod[u][k * S::W + i + 1], v[i], v[i + 1]);
@@ -265,14 +309,23 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
           if (cur >= 0) close_seg(cur, seg, e);
           // rows strictly between the previous nonzero's row and this one are empty
           const int32_t prev = (e == a) ? before : cur;
-          if (prev != rows[u]) zero_rows<PREC, RV>(Mout, Rp, (int64_t)prev + 1, rows[u], lig);
+          if (prev != rows[u]) {
+            zero_rows<PREC, RV>(Mout, Rp, (int64_t)prev + 1, rows[u], lig);
+            if constexpr (DUAL) zero_rows<PREC, RV>(Mf, Rp, (int64_t)prev + 1, rows[u], lig);
+          }
           cur = rows[u];
           seg = e;
 #pragma unroll
           for (int i = 0; i < S::NV; ++i) acc[i] = 0.f;
+#pragma unroll
+          for (int i = 0; i < NVF; ++i) accf[i] = 0.f;
         }
 #pragma unroll
         for (int i = 0; i < S::NV; i += 2) add2_inplace(acc[i], acc[i + 1], prod[u][i], prod[u][i + 1]);
+        if constexpr (DUAL) {
+#pragma unroll
+          for (int i = 0; i < NVF; i += 2) add2_inplace(accf[i], accf[i + 1], prodf[u][i], prodf[u][i + 1]);
+        }
       }
     }
   };
@@ -406,7 +459,10 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
   }
   if (cur >= 0) {
     close_seg(cur, seg, b);
-    if (b == nnz) zero_rows<PREC, RV>(Mout, Rp, (int64_t)cur + 1, I, lig);
+    if (b == nnz) {
+      zero_rows<PREC, RV>(Mout, Rp, (int64_t)cur + 1, I, lig);
+      if constexpr (DUAL) zero_rows<PREC, RV>(Mf, Rp, (int64_t)cur + 1, I, lig);
+    }
   }
   if (lig == 0) wp.flags[g] = flags;
   __syncwarp();
@@ -416,25 +472,34 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
     bool run_valid = false, run_tile_left = false;
     int32_t run_row = -1;
     float run[S::NV];
+    float runf[NVF];
     auto finish = [&](bool right_open_at_tile) {
+      int64_t off;
       float* dst;
+      float* dstf = nullptr;
       if (run_tile_left || right_open_at_tile) {
         const int slot = run_tile_left ? 0 : 1;
-        dst = carry + (tile * 2 + slot) * (int64_t)Rp;
+        off = (tile * 2 + slot) * (int64_t)Rp;
+        dst = carry + off;
+        if constexpr (DUAL) dstf = carryf + off;
       } else {
-        dst = Mout + (int64_t)run_row * Rp;
+        off = (int64_t)run_row * Rp;
+        dst = Mout + off;
+        if constexpr (DUAL) dstf = Mf + off;
       }
 #pragma unroll
       for (int k = 0; k < S::CPL; ++k) {
         int c0;
         lane_cols<PREC, RV>(lig, k, c0);
         store_row_chunk<S::W>(dst, c0, run + k * S::W);
+        if constexpr (DUAL) store_row_chunk<S::W>(dstf, c0, runf + k * S::W);
       }
     };
     for (int gg = 0; gg < S::G; ++gg) {
       const int f = wp.flags[gg];
       if (f & 1) {
         const float* src = &wp.acc[0][0] + gg * Rp;
+        const float* srcf = DUAL ? &wpf->acc[0][0] + gg * Rp : nullptr;
         if (!run_valid) {
           run_valid = true;
           run_tile_left = true;  // only possible for the tile's first group
@@ -445,6 +510,10 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
             lane_cols<PREC, RV>(lig, k, c0);
 #pragma unroll
             for (int i = 0; i < S::W; ++i) run[k * S::W + i] = src[c0 + i];
+            if constexpr (DUAL) {
+#pragma unroll
+              for (int i = 0; i < S::W; ++i) runf[k * S::W + i] = srcf[c0 + i];
+            }
           }
         } else {
 #pragma unroll
@@ -453,6 +522,10 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
             lane_cols<PREC, RV>(lig, k, c0);
 #pragma unroll
             for (int i = 0; i < S::W; ++i) run[k * S::W + i] += src[c0 + i];
+            if constexpr (DUAL) {
+#pragma unroll
+              for (int i = 0; i < S::W; ++i) runf[k * S::W + i] += srcf[c0 + i];
+            }
           }
         }
         if (!(f & 2)) {
@@ -471,6 +544,11 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
           lane_cols<PREC, RV>(lig, k, c0);
 #pragma unroll
           for (int i = 0; i < S::W; ++i) run[k * S::W + i] = src[c0 + i];
+          if constexpr (DUAL) {
+            const float* srcf = &wpf->acc[1][0] + gg * Rp;
+#pragma unroll
+            for (int i = 0; i < S::W; ++i) runf[k * S::W + i] = srcf[c0 + i];
+          }
         }
       }
     }
@@ -492,6 +570,24 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (TileShape<PREC, RV>::MIN
   if (gt >= total_tiles) return;
   const int j = njobs > 1 ? find_job(tile_base, njobs, gt) : 0;
   mttkrp_tile<PREC, RV, NO>(descs + j, gt - tile_base[j], pieces[warp], stage[warp]);
+}
+
+// The objective's FP32-gather MTTKRP of a mode and the BF16-gather MTTKRP of that mode's next step
+// in one pass over its nonzeros (mttkrp_tile with DUAL): dB is the mode's descriptor (BF16 tiling,
+// output M, partial buffer), dF the objective's (FP32 master factors, its own output and partial
+// buffer). One job per launch; 16 resident warps per SM (the two product chains need the
+// registers).
+template <int RV, int NO>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 16 / kWarpsPerBlock)
+    mttkrp_dual_kernel(const StepDesc* __restrict__ dB, const StepDesc* __restrict__ dF, int64_t total_tiles) {
+  __shared__ WarpPieces pieces[kWarpsPerBlock];
+  __shared__ WarpPieces piecesf[kWarpsPerBlock];
+  constexpr int kSlot = TileShape<1, RV>::stage_words(NO);
+  __shared__ __align__(16) int32_t stage[kWarpsPerBlock][SACD_MTTKRP_STAGED ? 2 * kSlot : 4];
+  const int warp = threadIdx.x >> 5;
+  const int64_t gt = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (gt >= total_tiles) return;
+  mttkrp_tile<1, RV, NO, true>(dB, gt, pieces[warp], stage[warp], dF, &piecesf[warp]);
 }
 
 // Rows split across tiles, with few partials: one warp per row, partials summed in tile order.
@@ -625,6 +721,19 @@ void launch_mttkrp(const StepDesc* d_descs, const int64_t* d_tile_base, int njob
     launch_mttkrp_prec<0>(d_descs, d_tile_base, njobs, total_tiles, rv, nother, st);
   else
     launch_mttkrp_prec<1>(d_descs, d_tile_base, njobs, total_tiles, rv, nother, st);
+}
+
+bool mttkrp_dual_supported(int rv, int nother) { return (rv == 4 || rv == 8) && (nother == 2 || nother == 3); }
+
+void launch_mttkrp_dual(const StepDesc* dB, const StepDesc* dF, int64_t total_tiles, int rv, int nother,
+                        cudaStream_t st) {
+  if (total_tiles <= 0) return;
+  const unsigned blocks = (unsigned)((total_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  const int T = kWarpsPerBlock * 32;
+  if (rv == 4 && nother == 2) mttkrp_dual_kernel<4, 2><<<blocks, T, 0, st>>>(dB, dF, total_tiles);
+  else if (rv == 4 && nother == 3) mttkrp_dual_kernel<4, 3><<<blocks, T, 0, st>>>(dB, dF, total_tiles);
+  else if (rv == 8 && nother == 2) mttkrp_dual_kernel<8, 2><<<blocks, T, 0, st>>>(dB, dF, total_tiles);
+  else if (rv == 8 && nother == 3) mttkrp_dual_kernel<8, 3><<<blocks, T, 0, st>>>(dB, dF, total_tiles);
 }
 
 // row -> split entry map (-1 elsewhere; the caller fills it with -1 first)

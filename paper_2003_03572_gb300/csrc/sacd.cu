@@ -123,6 +123,15 @@ struct sacd_ctx {
   StepDesc* ddesc = nullptr;
   float* Mfit = nullptr;  // BF16 mode: MTTKRP of mode fit_mode from the FP32 master factors (objective)
   int fit_mode = 0;       // the mode whose M the objective contracts with its factor
+  // BF16 mode with fit_mode 0 and a supported width: the objective's MTTKRP also forms mode 0's
+  // BF16-gather MTTKRP of the next step in the same pass (launch_mttkrp_dual). The objective's
+  // partials then go to buffers of their own, and mpre says that m[0].M and its tile partials in
+  // `carry` are current (no factor has changed and no other MTTKRP has run since): the next step
+  // of mode 0 skips its MTTKRP kernel.
+  bool dual_fit = false;
+  bool mpre = false;
+  float* carryF = nullptr;
+  float* carry2F = nullptr;
   FitDesc hfit;
   FitDesc* dfit = nullptr;
   double* fitpart = nullptr;
@@ -132,6 +141,8 @@ struct sacd_ctx {
   int64_t fit_blocks = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph_pre = nullptr;  // the iteration with mode 0's MTTKRP kernel left out (mpre)
+  cudaGraphExec_t gexec_pre = nullptr;
   // second stream and events for the graph's parallel branch (Gram and H of the next mode
   // run beside the next mode's MTTKRP)
   cudaStream_t side = nullptr;
@@ -252,13 +263,13 @@ struct KScope {
 // StepDesc::rowfix) and writes them into M, so only the chunk level runs here; without it (M
 // needed on its own, e.g. for the objective) every level runs.
 void enqueue_mttkrp_desc(sacd_ctx* c, int n, const StepDesc* dd, int prec, int rv, float* Mout, bool fold,
-                         int cls_main, int cls_fix) {
+                         int cls_main, int cls_fix, bool skip_main = false) {
   ModeData& md = c->m[n];
   if (c->nnz == 0) {
     cudaMemsetAsync(Mout, 0, (size_t)md.I * c->Rp * sizeof(float), c->st);
     return;
   }
-  {
+  if (!skip_main) {  // skipped when the dual pass of the objective has already formed M and its partials
     KScope k(c, cls_main);
     launch_mttkrp(dd, c->zero64, 1, md.ntiles, prec, rv, c->N - 1, c->st);
   }
@@ -273,8 +284,8 @@ void enqueue_mttkrp_desc(sacd_ctx* c, int n, const StepDesc* dd, int prec, int r
   }
 }
 
-void enqueue_mttkrp(sacd_ctx* c, int n, bool fold) {
-  enqueue_mttkrp_desc(c, n, c->ddesc + n, c->prec, c->rv, c->m[n].M, fold, K_MTTKRP, K_FIXUP);
+void enqueue_mttkrp(sacd_ctx* c, int n, bool fold, bool skip_main = false) {
+  enqueue_mttkrp_desc(c, n, c->ddesc + n, c->prec, c->rv, c->m[n].M, fold, K_MTTKRP, K_FIXUP, skip_main);
 }
 
 // The M that the objective contracts with factor fit_mode (<X, model> = sum of A_n .* M_n for any
@@ -282,10 +293,24 @@ void enqueue_mttkrp(sacd_ctx* c, int n, bool fold) {
 // last mode step). BF16-gather mode: an MTTKRP from FP32 gathers of the FP32 master factors (the
 // factors the caller gets back), into Mfit, every time: the BF16-gathered M of the mode steps is
 // not the model of those factors. It runs on the longest mode, whose other factors are the
-// smallest (the most gathered rows served from L1/L2).
+// smallest (the most gathered rows served from L1/L2). With dual_fit the same pass also forms mode
+// 0's BF16-gather MTTKRP of the next step (mpre), for a context's own objective and in a batch alike,
+// so that the objective's value does not depend on the path.
 void enqueue_fit_mttkrp(sacd_ctx* c) {
   if (c->prec == SACD_BF16_GATHER) {
-    enqueue_mttkrp_desc(c, c->fit_mode, c->ddesc + c->N, SACD_FP32, c->Rp / 4, c->Mfit, false, K_FIT_MTTKRP,
+    const int L = c->fit_mode;
+    if (c->dual_fit && c->nnz > 0) {
+      {
+        KScope k(c, K_FIT_MTTKRP);
+        launch_mttkrp_dual(c->ddesc + L, c->ddesc + c->N, c->m[L].ntiles, c->rv, c->N - 1, c->st);
+      }
+      // the objective's split rows from its own partials; mode 0's stay in `carry` for its step
+      enqueue_mttkrp_desc(c, L, c->ddesc + c->N, SACD_FP32, c->Rp / 4, c->Mfit, false, K_FIT_MTTKRP, K_FIT_MTTKRP,
+                          true);
+      c->mpre = true;
+      return;
+    }
+    enqueue_mttkrp_desc(c, L, c->ddesc + c->N, SACD_FP32, c->Rp / 4, c->Mfit, false, K_FIT_MTTKRP,
                         K_FIT_MTTKRP);
   } else if (!c->mlast_valid) {
     enqueue_mttkrp(c, c->N - 1, false);
@@ -322,11 +347,13 @@ void enqueue_select_update(sacd_ctx* c, int n, cudaStream_t st) {
 
 void enqueue_step(sacd_ctx* c, int n) {
   StepDesc* dd = c->ddesc + n;
+  const bool pre = c->mpre && n == c->fit_mode;  // M and its partials formed by the objective's pass
+  c->mpre = false;                               // any step changes a factor
   {
     KScope k(c, K_HL);
     launch_hl(dd, 1, c->st);
   }
-  enqueue_mttkrp(c, n, true);
+  enqueue_mttkrp(c, n, true, pre);
   enqueue_select_update(c, n, c->st);
   enqueue_gram(c, n);
 }
@@ -334,8 +361,9 @@ void enqueue_step(sacd_ctx* c, int n) {
 // One outer iteration as a DAG, captured into the CUDA graph. Main stream: MTTKRP(n) ->
 // pass1(n) -> pass2(n) -> MTTKRP(n+1) ...; side stream: Gram(n) -> H/L(n+1), which only needs
 // the updated factor n and the Grams, so it overlaps MTTKRP(n+1). Same kernels and inputs as the
-// sequential order, so the results are identical.
-void enqueue_iteration_dag(sacd_ctx* c) {
+// sequential order, so the results are identical. With `pre0`, mode 0's MTTKRP kernel is left out
+// (the objective's dual pass has formed it: mpre).
+void enqueue_iteration_dag(sacd_ctx* c, bool pre0 = false) {
   cudaEvent_t* ev = c->ev;  // [0] fork, [1..N] H ready, [N+1..2N] pass2 done, [2N+1] join
   const int N = c->N;
   cudaEventRecord(ev[0], c->st);
@@ -345,7 +373,7 @@ void enqueue_iteration_dag(sacd_ctx* c) {
   for (int n = 0; n < N; ++n) {
     ModeData& md = c->m[n];
     StepDesc* dd = c->ddesc + n;
-    enqueue_mttkrp(c, n, true);
+    enqueue_mttkrp(c, n, true, pre0 && n == 0);
     cudaStreamWaitEvent(c->st, ev[1 + n], 0);
     enqueue_select_update(c, n, c->st);
     cudaEventRecord(ev[N + 1 + n], c->st);
@@ -364,8 +392,13 @@ void enqueue_iteration_dag(sacd_ctx* c) {
 void invalidate_graph(sacd_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->gexec_pre) cudaGraphExecDestroy(c->gexec_pre);
+  if (c->graph_pre) cudaGraphDestroy(c->graph_pre);
   c->gexec = nullptr;
   c->graph = nullptr;
+  c->gexec_pre = nullptr;
+  c->graph_pre = nullptr;
+  c->mpre = false;  // descriptors or tiles may have changed
 }
 
 // BF16 mode: the objective's MTTKRP of mode fit_mode gathers FP32 rows of the master factors. It
@@ -385,6 +418,10 @@ void fill_fit_desc(sacd_ctx* c) {
   d.sub = d.tile / groups32;
   d.M = c->Mfit;
   d.mask = nullptr;
+  if (c->dual_fit) {  // the objective's partials apart from the mode's (which the dual pass keeps)
+    d.carry = c->carryF;
+    d.carry2 = c->carry2F;
+  }
   c->hdesc[c->N] = d;
 }
 
@@ -869,6 +906,11 @@ sacd_status create_impl(const sacd_config* cfg, sacd_ctx** out) {
     const int64_t If = c->m[c->fit_mode].I;
     TRY(dalloc(c, &c->Mfit, (size_t)If * Rp));
     CK(cudaMemsetAsync(c->Mfit, 0, sizeof(float) * If * Rp, c->st));
+    c->dual_fit = c->fit_mode == 0 && mttkrp_dual_supported(c->rv, N - 1);
+    if (c->dual_fit) {
+      TRY(dalloc(c, &c->carryF, (size_t)c->carry_cap * 2 * Rp));
+      TRY(dalloc(c, &c->carry2F, (size_t)c->carry2_cap * Rp));
+    }
   }
   for (int n = 0; n < N; ++n) {
     ModeData& md = c->m[n];
@@ -1021,16 +1063,25 @@ sacd_status sacd_iterate(sacd_ctx* c, int32_t iters) {
       for (int n = 0; n < c->N; ++n) enqueue_step(c, n);
     CK(cudaGetLastError());
   } else {
-    if (!c->gexec) {
+    auto capture = [c](bool pre0, cudaGraph_t* graph, cudaGraphExec_t* exec) -> sacd_status {
       CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-      enqueue_iteration_dag(c);
+      enqueue_iteration_dag(c, pre0);
       cudaGraph_t g = nullptr;
       const cudaError_t e = cudaStreamEndCapture(c->st, &g);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
-      c->graph = g;
-      CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
+      *graph = g;
+      CK(cudaGraphInstantiate(exec, g, 0));
+      return SACD_OK;
+    };
+    int it = 0;
+    if (c->mpre && c->fit_mode == 0) {  // the first iteration's mode-0 MTTKRP is already formed
+      if (!c->gexec_pre) TRY(capture(true, &c->graph_pre, &c->gexec_pre));
+      CK(cudaGraphLaunch(c->gexec_pre, c->st));
+      it = 1;
     }
-    for (int it = 0; it < iters; ++it) CK(cudaGraphLaunch(c->gexec, c->st));
+    c->mpre = false;
+    if (it < iters && !c->gexec) TRY(capture(false, &c->graph, &c->gexec));
+    for (; it < iters; ++it) CK(cudaGraphLaunch(c->gexec, c->st));
   }
   c->last_mode = c->N - 1;
   c->mlast_valid = true;
@@ -1082,6 +1133,7 @@ sacd_status sacd_set_factor(sacd_ctx* c, int32_t mode, const float* host_in) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   if (mode != c->N - 1) c->mlast_valid = false;
+  c->mpre = false;
   return SACD_OK;
 }
 
@@ -1319,6 +1371,7 @@ sacd_status sacd_load(sacd_ctx* c, const void* host_buf, size_t bytes) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   c->mlast_valid = false;
+  c->mpre = false;
   return SACD_OK;
 }
 
@@ -1336,13 +1389,17 @@ sacd_status sacd_set_tiling(sacd_ctx* c, int32_t mode, int32_t sub) {
     ModeData& md = c->m[mode];
     if (md.ntiles > c->carry_cap) {
       drop_alloc(c, c->carry, sizeof(float) * c->carry_cap * 2 * c->Rp);
+      if (c->carryF) drop_alloc(c, c->carryF, sizeof(float) * c->carry_cap * 2 * c->Rp);
       c->carry_cap = md.ntiles;
       TRY(dalloc(c, &c->carry, (size_t)c->carry_cap * 2 * c->Rp));
+      if (c->dual_fit) TRY(dalloc(c, &c->carryF, (size_t)c->carry_cap * 2 * c->Rp));
     }
     if (md.nchunks > c->carry2_cap) {
       drop_alloc(c, c->carry2, sizeof(float) * c->carry2_cap * c->Rp);
+      if (c->carry2F) drop_alloc(c, c->carry2F, sizeof(float) * c->carry2_cap * c->Rp);
       c->carry2_cap = md.nchunks;
       TRY(dalloc(c, &c->carry2, (size_t)c->carry2_cap * c->Rp));
+      if (c->dual_fit) TRY(dalloc(c, &c->carry2F, (size_t)c->carry2_cap * c->Rp));
     }
     for (int n = 0; n < c->N; ++n) {
       StepDesc& d = c->hdesc[n];
@@ -1752,6 +1809,7 @@ sacd_status sacd_batch_iterate(sacd_batch* b, int32_t iters) {
   for (sacd_ctx* c : b->jobs) {
     c->last_mode = c->N - 1;
     c->mlast_valid = true;
+    c->mpre = false;
   }
   return SACD_OK;
 }
@@ -1847,7 +1905,10 @@ int64_t estimate_bytes(const sacd_config* c) {
                        rows * 4;  // + the row -> split entry maps
   const int64_t tiles = nnz / 32 + 1;
   const int64_t gram_blocks = std::min<int64_t>((Imax + 4096 / Rp - 1) / (4096 / Rp), 4 * 152);
-  const int64_t scratch = Imax * Rp * 6 + tiles * (2 * Rp * 4 + 16) + gram_blocks * Rp * Rp * 8 + (1 << 20);
+  // tile partials (a second set for the objective's own in BF16 mode), chunk sums, Gram partials
+  const int64_t partial_sets = c->precision == SACD_BF16_GATHER ? 2 : 1;
+  const int64_t scratch =
+      Imax * Rp * 6 + partial_sets * tiles * (2 * Rp * 4 + 16) + gram_blocks * Rp * Rp * 8 + (1 << 20);
   const int64_t temps = nnz * (12 * N + 64) + (nnz / 2048 + 1) * 256 * 12;
   return (csf + facs + scratch + temps) * 11 / 10;
 }
@@ -2088,6 +2149,7 @@ sacd_status sacd_server_step(sacd_server* s, int32_t* n_active, int32_t* n_waiti
       j->done_iters++;
       j->ctx->last_mode = j->ctx->N - 1;
       j->ctx->mlast_valid = true;
+      j->ctx->mpre = false;
       if (j->done_iters < j->iters) {
         still.push_back(j);
         continue;

@@ -374,6 +374,53 @@ def test_bf16_gather_mode():
         assert dfit <= 5e-3
 
 
+DUAL_CASES = [CASES[1], CASES[3], ((300, 200, 40, 20), 20_000, "zipf", 1.2, 32), CASES[2]]
+
+
+@pytest.mark.parametrize("case", DUAL_CASES, ids=ids)
+def test_bf16_objective_pass_feeds_the_next_step(case):
+    """BF16 gathers: when the objective's mode is mode 0, its FP32-gather MTTKRP also forms mode 0's
+    BF16-gather MTTKRP of the next step in the same pass. An objective after every iteration (graph
+    path) or after every eager iteration gives factors bit for bit equal to no objective at all;
+    the objective meets its bound at identical factors; a factor changed after the objective makes
+    the next step form its MTTKRP again. (The rank-16 case uses the separate pass.)"""
+    dims, nnz, dist, s, R = case
+    idx, vals, init = make_case(dims, nnz, dist, s, R)
+    cidx, cvals = O.coalesce(dims, idx, vals)
+    N = len(dims)
+    kw = dict(precision=S.SACD_BF16_GATHER)
+    with S.SaCD(dims, idx, vals, R, init, **kw) as a, S.SaCD(dims, idx, vals, R, init, **kw) as b, \
+            S.SaCD(dims, idx, vals, R, init, **kw) as c:
+        for it in range(4):
+            a.iterate(1)
+            a.fit()
+            b.iterate(1)
+            for n in range(N):
+                c.mode_step(n, want_count=False)
+            c.fit()
+        for n in range(N):
+            np.testing.assert_array_equal(a.factor(n), b.factor(n))
+            np.testing.assert_array_equal(c.factor(n), b.factor(n))
+        obj, fit = a.fit()
+        assert (obj, fit) == b.fit() == c.fit()
+        F = a.factors()
+        nx = O.norm_x_sq(cvals)
+        inner = O.inner_x_model(cidx, cvals, F)
+        mn = O.model_norm_sq(F)
+        assert abs(obj - (nx - 2.0 * inner + mn)) <= 2.0 * 2e-6 * abs(inner) + 1e-9 * mn + 1e-12 * nx
+        # a factor changed after the objective: mode 0's step must gather it
+        a.set_factor(1, 0.5 * a.factor(1))
+        b.set_factor(1, 0.5 * b.factor(1))
+        a.mode_step(0)
+        b.mode_step(0)
+        np.testing.assert_array_equal(a.factor(0), b.factor(0))
+        a.fit()
+        a.iterate(2)
+        b.iterate(2)
+        for n in range(N):
+            np.testing.assert_array_equal(a.factor(n), b.factor(n))
+
+
 @pytest.mark.parametrize("prec", [S.SACD_FP32, S.SACD_BF16_GATHER], ids=["fp32", "bf16"])
 @pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3]], ids=ids)
 def test_fit_at_identical_factors(case, prec):
