@@ -112,6 +112,12 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 #ifndef SACD_MTTKRP_MINB
 #define SACD_MTTKRP_MINB 0
 #endif
+// Resident warps per SM for rows of more than 4 floats per lane (BF16 gathers), measured on the
+// 50M-nonzero rank-64 tensor: 28 (72 registers, 84 bytes spilled) 4.77 ms per iteration, 24 (80,
+// 52 bytes) 4.84 ms, 20 (96, 8 bytes) 5.16 ms: more gathers in flight outweigh the spills.
+#ifndef SACD_MTTKRP_WIDE_WARPS
+#define SACD_MTTKRP_WIDE_WARPS 28
+#endif
 
 template <int PREC, int RV>
 struct TileShape {
@@ -121,8 +127,8 @@ struct TileShape {
   static constexpr int G = 32 / LPR;             // lane groups per warp
   static constexpr int NV = CPL * W;             // floats per lane
   static constexpr int U = SACD_MTTKRP_UNROLL ? SACD_MTTKRP_UNROLL : (NV <= 4 ? 4 : 2);
-  // resident warps per SM: 16 for rows of up to 4 floats per lane, 24 for wider ones
-  static constexpr int MINB = SACD_MTTKRP_MINB ? SACD_MTTKRP_MINB : (NV <= 4 ? 16 : 24) / kWarpsPerBlock;
+  // resident warps per SM: 16 for rows of up to 4 floats per lane, SACD_MTTKRP_WIDE_WARPS for wider ones
+  static constexpr int MINB = SACD_MTTKRP_MINB ? SACD_MTTKRP_MINB : (NV <= 4 ? 16 : SACD_MTTKRP_WIDE_WARPS) / kWarpsPerBlock;
   // nonzeros of a warp in one index stage (measured: 128 for the narrow rows, 64 for the wide
   // ones), and per lane group: whole 16-byte pieces and whole unroll steps
   static constexpr int SNNZ = SACD_MTTKRP_STAGE_NNZ ? SACD_MTTKRP_STAGE_NNZ : (NV <= 4 ? 128 : 64);
@@ -575,10 +581,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (TileShape<PREC, RV>::MIN
 // The objective's FP32-gather MTTKRP of a mode and the BF16-gather MTTKRP of that mode's next step
 // in one pass over its nonzeros (mttkrp_tile with DUAL): dB is the mode's descriptor (BF16 tiling,
 // output M, partial buffer), dF the objective's (FP32 master factors, its own output and partial
-// buffer). One job per launch; 16 resident warps per SM (the two product chains need the
-// registers).
+// buffer). One job per launch. Resident warps per SM, measured on the 50M-nonzero rank-64 tensor:
+// 20 (96 registers, 4 bytes spilled) beats 16 (127 registers, no spill) by 9% and 24 (80
+// registers, 100 bytes spilled) by 7%.
+#ifndef SACD_MTTKRP_DUAL_WARPS
+#define SACD_MTTKRP_DUAL_WARPS 20
+#endif
 template <int RV, int NO>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 16 / kWarpsPerBlock)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, SACD_MTTKRP_DUAL_WARPS / kWarpsPerBlock)
     mttkrp_dual_kernel(const StepDesc* __restrict__ dB, const StepDesc* __restrict__ dF, int64_t total_tiles) {
   __shared__ WarpPieces pieces[kWarpsPerBlock];
   __shared__ WarpPieces piecesf[kWarpsPerBlock];
