@@ -467,6 +467,7 @@ def measure_workload(w, args, dev, stream, ws, rank, local, steps, cpu_leg):
     h_out = [torch.empty(a.shape, dtype=torch.float32).pin_memory() for a in init]
     iters = w.iters
     e2e_times = []
+    e2e_parts = []
     clk2 = ClockSampler(local)
     clk2.start()
     for rep in range(max(args.e2e_reps, 1) + 1):
@@ -475,6 +476,7 @@ def measure_workload(w, args, dev, stream, ws, rank, local, steps, cpu_leg):
         t0 = time.perf_counter()
         ctx = S.sacd_create(w.dims, [t.numpy() for t in h_idx], h_vals.numpy(), w.rank,
                             [t.numpy() for t in h_init], precision=prec, stream=stream.cuda_stream)
+        t_created = time.perf_counter()  # host time at which create returned (its work may still run)
         S.sacd_iterate(ctx, iters)
         e2e_fit = S.sacd_fit(ctx)
         for n in range(N):
@@ -483,6 +485,7 @@ def measure_workload(w, args, dev, stream, ws, rank, local, steps, cpu_leg):
         t1 = time.perf_counter()
         if rep > 0:  # first solve is a warm-up (allocator, graph instantiation)
             e2e_times.append(t1 - t0)
+            e2e_parts.append((t_created - t0, t1 - t_created))
     e2e_clocks = clk2.stop()
     e2e_s = aggregate_over_ranks(statistics.median(e2e_times), ws, dev)
     h2d = int(len(vals) * (4 * N + 4) + sum(a.nbytes for a in init))
@@ -498,6 +501,8 @@ def measure_workload(w, args, dev, stream, ws, rank, local, steps, cpu_leg):
         "mode_steps_per_step": N * iters,
         "seconds_per_solve": e2e_s,
         "solve_seconds": [round(t, 5) for t in e2e_times],
+        "create_return_seconds": [round(a, 5) for a, _ in e2e_parts],
+        "after_create_seconds": [round(b, 5) for _, b in e2e_parts],
         "final_fit": e2e_fit[1],
         "clocks": e2e_clocks,
     }
@@ -816,7 +821,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=None, help="one workload only (default: the headline and the others)")
     ap.add_argument("--min-seconds", type=float, default=1.0, help="repeat the K-step timed region until this long")
-    ap.add_argument("--e2e-reps", type=int, default=3)
+    ap.add_argument("--e2e-reps", type=int, default=4,
+                    help="timed solves after one warm-up solve (consecutive solves alternate between two "
+                         "durations; an even count keeps the median from depending on which comes first)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-jobs", action="store_true", help="skip the batched and served sub-records")
     ap.add_argument("--kernels-only", action="store_true", help="skip the end-to-end and CPU legs (profiling)")
