@@ -119,6 +119,33 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 #define SACD_MTTKRP_WIDE_WARPS 28
 #endif
 
+// Staged index rows of the lane groups start `cp` words apart; each group reads `rw` consecutive
+// words of its row at once. The number of groups whose words fall in the busiest bank (the
+// wavefronts of one such read when the groups' addresses differ).
+__host__ __device__ constexpr int stage_bank_load(int g, int cp, int rw) {
+  int worst = 0;
+  for (int b = 0; b < 32; ++b) {
+    int hits = 0;
+    for (int x = 0; x < g; ++x)
+      if (((b - x * cp) % 32 + 32) % 32 < rw) ++hits;
+    worst = hits > worst ? hits : worst;
+  }
+  return worst;
+}
+// The row pitch of the stage: among sc, sc + 4, ..., sc + 28 (multiples of 4 keep every row
+// 16-byte aligned for cp.async) the one with the lightest busiest bank, the smallest on ties.
+__host__ __device__ constexpr int stage_pitch(int g, int sc, int rw) {
+  int best = sc, cost = stage_bank_load(g, sc, rw);
+  for (int k = 1; k < 8; ++k) {
+    const int c = stage_bank_load(g, sc + 4 * k, rw);
+    if (c < cost) {
+      cost = c;
+      best = sc + 4 * k;
+    }
+  }
+  return best;
+}
+
 template <int PREC, int RV>
 struct TileShape {
   static constexpr int W = GatherVec<PREC>::W;
@@ -134,7 +161,16 @@ struct TileShape {
   static constexpr int SNNZ = SACD_MTTKRP_STAGE_NNZ ? SACD_MTTKRP_STAGE_NNZ : (NV <= 4 ? 128 : 64);
   static constexpr int SMIN = U > 4 ? U : 4;
   static constexpr int SC = SNNZ / G > SMIN ? SNNZ / G : SMIN;
-  __host__ __device__ static constexpr int stage_words(int nother) { return (2 + nother) * G * SC; }
+  // Words between the lane groups' rows of a staged array. The groups read their next RW words
+  // (one int4, int2 or int32 per array) at once. 8-byte and 4-byte reads are served for the whole
+  // warp together: at a pitch of SC (a multiple of 16 from 16 up) groups g and g + 2 share banks
+  // and each index read took two wavefronts (ncu, BF16 rows at R = 64), so those take the pitch
+  // search (the BF16 mode-step and objective passes gained 1.8% and 2.3%). 16-byte reads are served
+  // a quarter-warp at a time, where the groups are already in distinct banks at pitch SC; padding
+  // them made the FP32 kernel at R = 32 4% slower, so they keep SC.
+  static constexpr int RW = (U == 4 || U == 2) ? U : 1;
+  static constexpr int CP = RW == 4 ? SC : stage_pitch(G, SC, RW);
+  __host__ __device__ static constexpr int stage_words(int nother) { return (2 + nother) * G * CP; }
 };
 
 template <int NV>
@@ -342,10 +378,12 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
    if (staged) {
     constexpr int NA = 2 + NO;  // staged arrays: rows, values, other-mode indices
     constexpr int C = S::SC;                    // nonzeros per lane group per stage
+    constexpr int CP = S::CP;                   // words between lane groups' rows
     constexpr int QPG = C / 4;                  // 16-byte pieces per lane group and array
     constexpr int NQ = NA * S::G * QPG;         // pieces per stage
     constexpr int SLOT = S::stage_words(NA - 2);  // int32 words per stage
-    static_assert(C % 4 == 0 && C % kUnroll == 0, "a stage holds whole 16-byte pieces and unroll steps");
+    static_assert(C % 4 == 0 && C % kUnroll == 0 && CP % 4 == 0 && CP >= C,
+                  "a stage holds whole 16-byte pieces and unroll steps, rows 16-byte aligned");
     const int32_t* cidx0 = dp->cidx;
     const int nch = (sub + C - 1) / C;
     auto issue = [&](int k) {
@@ -359,7 +397,7 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
         const int valid = max(0, min(4, bg - e));
         const int32_t* arr = m == 0 ? rowid
                            : (m == 1 ? reinterpret_cast<const int32_t*>(val) : cidx0 + (int64_t)(m - 2) * cstride);
-        cp_async16(dst0 + (m * S::G + gg) * C + 4 * p, valid > 0 ? arr + e : arr, valid * 4);
+        cp_async16(dst0 + (m * S::G + gg) * CP + 4 * p, valid > 0 ? arr + e : arr, valid * 4);
       }
       cp_async_commit();
     };
@@ -377,33 +415,33 @@ __device__ void mttkrp_tile(const StepDesc* __restrict__ dp, int64_t tile, WarpP
         uint32_t ix[MAXO][kUnroll];
         // o is a multiple of kUnroll and every array row starts 16-byte aligned
         if constexpr (kUnroll == 4) {
-          const int4 r4 = *reinterpret_cast<const int4*>(sb + (0 * S::G + g) * C + o);
-          const int4 x4 = *reinterpret_cast<const int4*>(sb + (1 * S::G + g) * C + o);
+          const int4 r4 = *reinterpret_cast<const int4*>(sb + (0 * S::G + g) * CP + o);
+          const int4 x4 = *reinterpret_cast<const int4*>(sb + (1 * S::G + g) * CP + o);
           rows[0] = r4.x; rows[1] = r4.y; rows[2] = r4.z; rows[3] = r4.w;
           xs[0] = __int_as_float(x4.x); xs[1] = __int_as_float(x4.y);
           xs[2] = __int_as_float(x4.z); xs[3] = __int_as_float(x4.w);
 #pragma unroll
           for (int m = 0; m < MAXO; ++m) {
-            const int4 c4 = *reinterpret_cast<const int4*>(sb + ((2 + m) * S::G + g) * C + o);
+            const int4 c4 = *reinterpret_cast<const int4*>(sb + ((2 + m) * S::G + g) * CP + o);
             ix[m][0] = c4.x; ix[m][1] = c4.y; ix[m][2] = c4.z; ix[m][3] = c4.w;
           }
         } else if constexpr (kUnroll == 2) {
-          const int2 r2 = *reinterpret_cast<const int2*>(sb + (0 * S::G + g) * C + o);
-          const int2 x2 = *reinterpret_cast<const int2*>(sb + (1 * S::G + g) * C + o);
+          const int2 r2 = *reinterpret_cast<const int2*>(sb + (0 * S::G + g) * CP + o);
+          const int2 x2 = *reinterpret_cast<const int2*>(sb + (1 * S::G + g) * CP + o);
           rows[0] = r2.x; rows[1] = r2.y;
           xs[0] = __int_as_float(x2.x); xs[1] = __int_as_float(x2.y);
 #pragma unroll
           for (int m = 0; m < MAXO; ++m) {
-            const int2 c2 = *reinterpret_cast<const int2*>(sb + ((2 + m) * S::G + g) * C + o);
+            const int2 c2 = *reinterpret_cast<const int2*>(sb + ((2 + m) * S::G + g) * CP + o);
             ix[m][0] = c2.x; ix[m][1] = c2.y;
           }
         } else {
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
-            rows[u] = sb[(0 * S::G + g) * C + o + u];
-            xs[u] = __int_as_float(sb[(1 * S::G + g) * C + o + u]);
+            rows[u] = sb[(0 * S::G + g) * CP + o + u];
+            xs[u] = __int_as_float(sb[(1 * S::G + g) * CP + o + u]);
 #pragma unroll
-            for (int m = 0; m < MAXO; ++m) ix[m][u] = (uint32_t)sb[((2 + m) * S::G + g) * C + o + u];
+            for (int m = 0; m < MAXO; ++m) ix[m][u] = (uint32_t)sb[((2 + m) * S::G + g) * CP + o + u];
           }
         }
         consume(e0, rows, xs, ix, ce);
