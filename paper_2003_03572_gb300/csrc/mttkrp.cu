@@ -162,12 +162,11 @@ struct TileShape {
   static constexpr int SMIN = U > 4 ? U : 4;
   static constexpr int SC = SNNZ / G > SMIN ? SNNZ / G : SMIN;
   // Words between the lane groups' rows of a staged array. The groups read their next RW words
-  // (one int4, int2 or int32 per array) at once. 8-byte and 4-byte reads are served for the whole
-  // warp together: at a pitch of SC (a multiple of 16 from 16 up) groups g and g + 2 share banks
-  // and each index read took two wavefronts (ncu, BF16 rows at R = 64), so those take the pitch
-  // search (the BF16 mode-step and objective passes gained 1.8% and 2.3%). 16-byte reads are served
-  // a quarter-warp at a time, where the groups are already in distinct banks at pitch SC; padding
-  // them made the FP32 kernel at R = 32 4% slower, so they keep SC.
+  // (one int4, int2 or int32 per array) at once. At a pitch of SC (a multiple of 16 from 16 up)
+  // groups g and g + 2 share banks: in the BF16 kernel at R = 64 (two words per read) every shared
+  // load took two wavefronts (ncu), so reads narrower than 16 bytes take the pitch search (the
+  // BF16 mode-step and objective passes gained 1.8% and 2.3%). Padding the 16-byte reads of the
+  // FP32 kernel at R = 32 made it 4% slower, so those keep SC.
   static constexpr int RW = (U == 4 || U == 2) ? U : 1;
   static constexpr int CP = RW == 4 ? SC : stage_pitch(G, SC, RW);
   __host__ __device__ static constexpr int stage_words(int nother) { return (2 + nother) * G * CP; }
