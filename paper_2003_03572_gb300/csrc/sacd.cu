@@ -1126,6 +1126,7 @@ sacd_status sacd_set_factor(sacd_ctx* c, int32_t mode, const float* host_in) {
   for (int64_t e = 0; e < I * c->R; ++e)
     if (!(host_in[e] >= 0.f) || !std::isfinite(host_in[e]))
       return fail(SACD_EINVAL, "factor values must be finite and >= 0");
+  c->mpre = false;  // before the factor changes, so that an error below cannot leave it set
   CK(cudaMemcpy2DAsync(c->m[mode].A, sizeof(float) * c->Rp, host_in, sizeof(float) * c->R, sizeof(float) * c->R, I,
                        cudaMemcpyHostToDevice, c->st));
   if (c->m[mode].A16) launch_to_bf16(c->m[mode].A, c->m[mode].A16, I * c->Rp, c->st);
@@ -1349,6 +1350,17 @@ sacd_status sacd_load(sacd_ctx* c, const void* host_buf, size_t bytes) {
   std::vector<double> st((size_t)N * ST_STRIDE);
   CK(cudaMemcpyAsync(st.data(), c->state, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  {  // every factor is checked before anything is copied: a rejected buffer leaves the context as it was
+    const char* q = p;
+    for (int n = 0; n < N; ++n) {
+      const float* a = reinterpret_cast<const float*>(q + 16);
+      for (int64_t e = 0; e < c->m[n].I * R; ++e)
+        if (!(a[e] >= 0.f) || !std::isfinite(a[e])) return fail(SACD_EINVAL, "factor values must be finite and >= 0");
+      q += 16 + 2 * sizeof(float) * (size_t)c->m[n].I * R;
+    }
+  }
+  c->mlast_valid = false;  // before the factors change, so that an error below cannot leave them set
+  c->mpre = false;
   for (int n = 0; n < N; ++n) {
     double s2[2];
     memcpy(s2, p, 16);
@@ -1356,9 +1368,6 @@ sacd_status sacd_load(sacd_ctx* c, const void* host_buf, size_t bytes) {
     st[(size_t)n * ST_STRIDE + ST_FIRST] = s2[1];
     p += 16;
     const size_t mb = sizeof(float) * (size_t)c->m[n].I * R;
-    const float* a = reinterpret_cast<const float*>(p);
-    for (int64_t e = 0; e < c->m[n].I * R; ++e)
-      if (!(a[e] >= 0.f) || !std::isfinite(a[e])) return fail(SACD_EINVAL, "factor values must be finite and >= 0");
     CK(cudaMemcpy2DAsync(c->m[n].A, sizeof(float) * c->Rp, p, sizeof(float) * R, sizeof(float) * R, c->m[n].I,
                          cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpy2DAsync(c->m[n].zprev, sizeof(float) * c->Rp, p + mb, sizeof(float) * R, sizeof(float) * R,
@@ -1379,6 +1388,8 @@ sacd_status sacd_set_tiling(sacd_ctx* c, int32_t mode, int32_t sub) {
   TRY(check_ctx(c));
   if (mode < 0 || mode >= c->N) return fail(SACD_EINVAL, "mode out of range");
   if (sub < 4 || sub > 1024 || (sub & 3)) return fail(SACD_EINVAL, "sub must be a multiple of 4 in [4, 1024]");
+  // the tile partials of the objective's pass may move or be dropped below, also on an error path
+  c->mpre = false;
   try {
     {
       TmpAllocs T(c->st);

@@ -50,3 +50,35 @@ def test_checkpoint_resume_is_bit_identical(prec):
     with S.SaCD(dims, tr_i, tr_v, R + 1, seed=1) as c:
         with pytest.raises(S.SacdError):
             c.load(state)  # another rank
+
+
+def test_rejected_state_leaves_the_context_unchanged():
+    """A state buffer whose last factor holds a negative value is rejected before anything is
+    copied: every factor of the context stays as it was, and the context then runs on exactly like
+    a twin that never saw the buffer."""
+    dims, R, tr_i, tr_v, _, _, init = split_case(R=16)
+    N = len(dims)
+    with S.SaCD(dims, tr_i, tr_v, R, init) as a, S.SaCD(dims, tr_i, tr_v, R, init) as b:
+        a.iterate(2)
+        b.iterate(2)
+        state = a.save()
+        saved_last = a.factor(N - 1).copy()
+        a.iterate(1)
+        b.iterate(1)
+        # layout: magic, N, R, nnz, dims; per mode ti^{k-1} and the first-visit flag, then the
+        # factor and z^{k-1}, I_n x R FP32 each
+        off = 24 + 8 * N + sum(16 + 8 * dims[n] * R for n in range(N - 1)) + 16
+        stored = np.frombuffer(state, np.float32, count=dims[N - 1] * R, offset=off).reshape(dims[N - 1], R)
+        np.testing.assert_array_equal(stored, saved_last)  # the offset points at the last factor
+        bad = bytearray(state)
+        bad[off:off + 4] = np.float32(-1.0).tobytes()
+        before = [a.factor(n).copy() for n in range(N)]
+        with pytest.raises(S.SacdError):
+            a.load(bytes(bad))
+        for n in range(N):
+            np.testing.assert_array_equal(a.factor(n), before[n])
+        a.iterate(2)
+        b.iterate(2)
+        for n in range(N):
+            np.testing.assert_array_equal(a.factor(n), b.factor(n))
+        assert a.fit() == b.fit()
