@@ -216,7 +216,8 @@ sacd_status sacd_pattern_distinctiveness(sacd_ctx* ctx, int32_t mode, double* pd
  * (cap >= that size) and waits. sacd_load restores a state saved from a context of the same
  * tensor shape, nonzero count and rank (the tensor itself is not saved: create the context from
  * the same tensor first). A resumed context continues bit-identically to one never interrupted.
- * Errors: SACD_EINVAL (size, magic, shape mismatch, bad factor values), SACD_ECUDA.
+ * Errors: SACD_EINVAL (size, magic, shape mismatch, bad factor values), SACD_ECUDA. sacd_load
+ * checks the whole buffer before it copies anything, so an SACD_EINVAL leaves the context unchanged.
  */
 sacd_status sacd_save(sacd_ctx* ctx, void* host_buf, size_t cap, size_t* bytes);
 sacd_status sacd_load(sacd_ctx* ctx, const void* host_buf, size_t bytes);
