@@ -25,6 +25,8 @@
 // (h_rr in place of L), whose larger steps need compensated gradients and corrections, keeps the
 // two-pass kernels. Each thread sums its z in an FP32 TwoSum pair and hands one FP64 value to the
 // block's fixed-order FP64 reduction (no FP64 arithmetic per element: FP64 is scarce here).
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "rowpass.cuh"
@@ -491,6 +493,9 @@ __global__ void __launch_bounds__(256, RT == 1 ? 4 : 2)
 }
 
 namespace {
+// Both caches below are filled on first use and guarded by g_occ_mu: contexts may be stepped from
+// several host threads at once.
+std::mutex g_occ_mu;
 int g_sm_count = 0;
 // resident blocks per SM for each (rows per thread, dynamic shared memory) used so far
 struct OccEntry {
@@ -503,6 +508,7 @@ int g_nocc = 0;
 
 template <int RT>
 int blocks_per_sm(size_t smem) {
+  std::lock_guard<std::mutex> lk(g_occ_mu);
   for (int i = 0; i < g_nocc; ++i)
     if (g_occ[i].rt == RT && g_occ[i].smem == smem) return g_occ[i].blocks;
   int nb = 0;
@@ -515,8 +521,8 @@ int blocks_per_sm(size_t smem) {
 
 template <int RT>
 cudaError_t launch_rt(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_chunks, size_t smem,
-                      GridBar* bar, long long budget, cudaStream_t st) {
-  const int64_t cap = (int64_t)g_sm_count * blocks_per_sm<RT>(smem);
+                      GridBar* bar, long long budget, int sms, cudaStream_t st) {
+  const int64_t cap = (int64_t)sms * blocks_per_sm<RT>(smem);
   const unsigned grid = (unsigned)std::min<int64_t>(total_chunks, cap);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -550,13 +556,18 @@ int selupd_choose_rt(int64_t rows, int Rp) {
 cudaError_t launch_selupd(const StepDesc* d_descs, const int64_t* d_base, int njobs, int64_t total_chunks, int rt,
                           size_t smem, GridBar* bar, long long budget, cudaStream_t st) {
   if (total_chunks <= 0) return cudaSuccess;
-  if (g_sm_count == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+  int sms = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    if (g_sm_count == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+    }
+    sms = g_sm_count;
   }
-  return rt == 4 ? launch_rt<4>(d_descs, d_base, njobs, total_chunks, smem, bar, budget, st)
-                 : launch_rt<1>(d_descs, d_base, njobs, total_chunks, smem, bar, budget, st);
+  return rt == 4 ? launch_rt<4>(d_descs, d_base, njobs, total_chunks, smem, bar, budget, sms, st)
+                 : launch_rt<1>(d_descs, d_base, njobs, total_chunks, smem, bar, budget, sms, st);
 }
 
 }  // namespace sacd
